@@ -1,0 +1,166 @@
+/*
+ * CPU oracle for the bit-reversed permutation: TEST INFRASTRUCTURE ONLY.
+ * See oracle.h for who may use it.  Plain C99 + POSIX threads, no compiler
+ * builtins, no tables, nothing shared with the GPU library.
+ *
+ * Every function is the plain definition from the Introduction of the paper
+ * (element i moves to rev_k(i), worked example for n = 8) or the swap loop
+ * of Listing 1.  No blocking, tiling or reordering is done here.
+ */
+#include "oracle.h"
+
+#include <pthread.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* Largest element we accept: the library's own limit is 16 bytes; the
+ * oracle is more permissive so that tests can use wider fingerprints. */
+#define ORACLE_MAX_ELEM 64
+
+static int bad_args(int k, int elem_bytes)
+{
+    return k < 0 || k > 40 || elem_bytes <= 0 || elem_bytes > ORACLE_MAX_ELEM;
+}
+
+/* Naive bitwise rev (Introduction, "Theta(b)" per index): take the bits of
+ * i from least to most significant and push each one onto the result from
+ * the right, so the first bit taken ends up most significant. */
+uint64_t oracle_rev_bits(uint64_t i, int k)
+{
+    uint64_t r = 0;
+    int j;
+    for (j = 0; j < k; ++j) {
+        r = (r << 1) | (i & 1u);
+        i >>= 1;
+    }
+    return r;
+}
+
+/* Definition of the permutation (Introduction): dst[rev(i)] <- src[i]. */
+int oracle_brev_oop(void *dst, const void *src, int k, int elem_bytes)
+{
+    uint64_t n, i;
+    unsigned char *d = (unsigned char *)dst;
+    const unsigned char *s = (const unsigned char *)src;
+    if (bad_args(k, elem_bytes) || (!dst || !src))
+        return -1;
+    n = (uint64_t)1 << k;
+    for (i = 0; i < n; ++i)
+        memcpy(d + oracle_rev_bits(i, k) * (uint64_t)elem_bytes,
+               s + i * (uint64_t)elem_bytes, (size_t)elem_bytes);
+    return 0;
+}
+
+/* Listing 1: in-place by swapping each unique pair (i, rev(i)) once; the
+ * comparison i < rev(i) stops a pair from being swapped back.  Listing 1
+ * skips i = 0 and i = n-1 because both are their own reverse; visiting
+ * them here is harmless (the comparison is false), so the loop runs over
+ * every index, which also makes k = 0 and k = 1 plain identities. */
+int oracle_brev_inplace(void *v, int k, int elem_bytes)
+{
+    uint64_t n, i, r;
+    unsigned char tmp[ORACLE_MAX_ELEM];
+    unsigned char *p = (unsigned char *)v;
+    if (bad_args(k, elem_bytes) || !v)
+        return -1;
+    n = (uint64_t)1 << k;
+    for (i = 0; i < n; ++i) {
+        r = oracle_rev_bits(i, k);
+        if (i < r) {
+            unsigned char *a = p + i * (uint64_t)elem_bytes;
+            unsigned char *b = p + r * (uint64_t)elem_bytes;
+            memcpy(tmp, a, (size_t)elem_bytes);
+            memcpy(a, b, (size_t)elem_bytes);
+            memcpy(b, tmp, (size_t)elem_bytes);
+        }
+    }
+    return 0;
+}
+
+struct oop_slice {
+    unsigned char *dst;
+    const unsigned char *src;
+    uint64_t begin, end;
+    int k, elem_bytes;
+};
+
+static void *oop_slice_run(void *arg)
+{
+    struct oop_slice *s = (struct oop_slice *)arg;
+    uint64_t i;
+    for (i = s->begin; i < s->end; ++i)
+        memcpy(s->dst + oracle_rev_bits(i, s->k) * (uint64_t)s->elem_bytes,
+               s->src + i * (uint64_t)s->elem_bytes, (size_t)s->elem_bytes);
+    return NULL;
+}
+
+/* The same definition as oracle_brev_oop, each thread taking one
+ * contiguous range of source indices.  Destinations of different i never
+ * coincide (rev is a bijection), so the threads never write the same
+ * element. */
+int oracle_brev_oop_mt(void *dst, const void *src, int k, int elem_bytes,
+                       int threads)
+{
+    uint64_t n, per;
+    int t, started = 0;
+    pthread_t *tid;
+    struct oop_slice *sl;
+    if (bad_args(k, elem_bytes) || !dst || !src || threads < 1)
+        return -1;
+    n = (uint64_t)1 << k;
+    if ((uint64_t)threads > n)
+        threads = (int)n;
+    tid = (pthread_t *)calloc((size_t)threads, sizeof(pthread_t));
+    sl = (struct oop_slice *)calloc((size_t)threads, sizeof(struct oop_slice));
+    if (!tid || !sl) {
+        free(tid);
+        free(sl);
+        return -1;
+    }
+    per = (n + (uint64_t)threads - 1) / (uint64_t)threads;
+    for (t = 0; t < threads; ++t) {
+        sl[t].dst = (unsigned char *)dst;
+        sl[t].src = (const unsigned char *)src;
+        sl[t].begin = per * (uint64_t)t < n ? per * (uint64_t)t : n;
+        sl[t].end = per * (uint64_t)(t + 1) < n ? per * (uint64_t)(t + 1) : n;
+        sl[t].k = k;
+        sl[t].elem_bytes = elem_bytes;
+    }
+    for (t = 1; t < threads; ++t) {
+        if (pthread_create(&tid[t], NULL, oop_slice_run, &sl[t]) != 0)
+            break;
+        ++started;
+    }
+    oop_slice_run(&sl[0]);
+    /* a slice whose thread could not start runs on this thread */
+    for (t = 1 + started; t < threads; ++t)
+        oop_slice_run(&sl[t]);
+    for (t = 1; t <= started; ++t)
+        pthread_join(tid[t], NULL);
+    free(tid);
+    free(sl);
+    return started + 1;
+}
+
+/* out[s] = src[rev(idx[s])]: the definition read at one output index at a
+ * time (the permutation is an involution, so the element landing at j is
+ * the one that started at rev(j)). */
+int oracle_brev_gather(void *out, const void *src, const uint64_t *idx,
+                       int64_t count, int k, int elem_bytes)
+{
+    int64_t s;
+    uint64_t n;
+    unsigned char *o = (unsigned char *)out;
+    const unsigned char *p = (const unsigned char *)src;
+    if (bad_args(k, elem_bytes) || count < 0 || (count && (!out || !src || !idx)))
+        return -1;
+    n = (uint64_t)1 << k;
+    for (s = 0; s < count; ++s) {
+        if (idx[s] >= n)
+            return -1;
+        memcpy(o + (uint64_t)s * (uint64_t)elem_bytes,
+               p + oracle_rev_bits(idx[s], k) * (uint64_t)elem_bytes,
+               (size_t)elem_bytes);
+    }
+    return 0;
+}

@@ -1,0 +1,56 @@
+/*
+ * CPU oracle for the bit-reversed permutation: TEST INFRASTRUCTURE ONLY.
+ *
+ * This header and oracle.c are the plain, slow, obviously correct statement
+ * of what the GPU library computes.  Only the test-suite, the smoke check in
+ * __graft_entry__.py and the CPU-baseline / reference legs of bench.py may
+ * load or call it.  The product path (the CUDA library and its Python
+ * binding) never includes, links or calls anything here, and this file
+ * includes nothing from the product.
+ *
+ * Definition followed (Introduction, the bit-reversed permutation and the
+ * n = 8 worked example): for an array of n = 2^k elements, the element at
+ * index i moves to index rev_k(i), where rev_k reverses the k-bit binary
+ * representation of i.  Elements are opaque blobs of E bytes; nothing is
+ * computed on them, only moved.
+ */
+#ifndef BREV_ORACLE_H
+#define BREV_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* rev_k(i): reverse the low k bits of i one bit at a time (the naive
+ * bitwise rev of the Introduction, Theta(k) per index).  Bits of i above
+ * bit k-1 are ignored.  k in [0, 63]; k = 0 gives 0. */
+uint64_t oracle_rev_bits(uint64_t i, int k);
+
+/* Out-of-place permutation: dst[rev_k(i)] = src[i] for every i < 2^k,
+ * element size elem_bytes.  dst and src must not overlap.
+ * Returns 0, or -1 on a bad argument. */
+int oracle_brev_oop(void *dst, const void *src, int k, int elem_bytes);
+
+/* In-place permutation by pair swaps (Listing 1: visit every index, swap
+ * v[i] with v[rev_k(i)] only when i < rev_k(i)).  Returns 0 or -1. */
+int oracle_brev_inplace(void *v, int k, int elem_bytes);
+
+/* The out-of-place definition again with the index range split over
+ * `threads` POSIX threads: only for timing on many host cores.  Same result
+ * as oracle_brev_oop.  Returns the number of threads used, or -1. */
+int oracle_brev_oop_mt(void *dst, const void *src, int k, int elem_bytes,
+                       int threads);
+
+/* Expected output at sampled positions: out[s] = src[rev_k(idx[s])] for
+ * s < count, where src holds the whole 2^k-element input.  Used to check
+ * full-size GPU runs at a sample of output indices. */
+int oracle_brev_gather(void *out, const void *src, const uint64_t *idx,
+                       int64_t count, int k, int elem_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BREV_ORACLE_H */

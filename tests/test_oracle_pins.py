@@ -1,0 +1,221 @@
+"""The CPU oracle pinned to the paper (runs without a GPU).
+
+Every check in ``pins.py`` runs against the oracle.  The mutation tests then
+plant typical mistakes in Python copies of the oracle (a dropped bit, a
+rotation for a reversal, a partly copied element, a missing comparison in
+the swap loop, an off-by-one shift) and require that some check fails for
+each, which shows the pins are strong enough to catch them.
+"""
+import numpy as np
+import pytest
+
+import pins
+
+
+class OracleImpl:
+    def __init__(self, oracle):
+        self.o = oracle
+
+    def rev(self, i, k):
+        return self.o.rev_bits(i, k)
+
+    def oop(self, src, k, E):
+        return self.o.brev_oop(src, k, E)
+
+    def inplace(self, buf, k, E):
+        return self.o.brev_inplace(buf, k, E)
+
+
+@pytest.fixture(scope="module")
+def impl(oracle_lib):
+    return OracleImpl(oracle_lib)
+
+
+def test_p1_worked_example(impl):
+    pins.check_worked_example(impl)
+
+
+def test_p2_even_odd_golden():
+    pins.check_even_odd_golden()
+
+
+def test_p3_brute_force(impl):
+    pins.check_brute_force(impl, kmax=12)
+
+
+def test_p4_involution(impl):
+    pins.check_involution(impl, ks=range(0, 19))
+
+
+def test_p4_involution_large(impl, oracle_lib):
+    # k = 22, 16-byte elements (64 MiB), out-of-place twice and in-place twice
+    k, E = 22, 16
+    x = pins.fingerprint_elems(1 << k, E, salt=22)
+    y = oracle_lib.brev_oop(x, k, E)
+    assert not np.array_equal(x, y)
+    assert np.array_equal(oracle_lib.brev_oop(y, k, E), x)
+    b = x.copy()
+    oracle_lib.brev_inplace(b, k, E)
+    assert np.array_equal(b, y)
+
+
+def test_p5_stockham(impl):
+    pins.check_stockham(impl, kmax=13)
+
+
+def test_p6_xor_induction(impl):
+    pins.check_xor_induction(impl, kmax=16)
+
+
+def test_p7_counts(impl):
+    pins.check_counts(impl, kmax=20)
+
+
+def test_p8_branch_and_bound_classes(impl):
+    pins.check_classes(impl, kmax=12)
+
+
+def test_p9_concatenation(impl):
+    pins.check_concatenation(impl)
+
+
+def test_p10_odd_k(impl):
+    pins.check_odd_k(impl)
+
+
+def test_p11_cobra_schedule(impl):
+    pins.check_cobra_schedule(impl, kmax=11)
+
+
+def test_p12_recursive_square(impl):
+    pins.check_recursive_square(impl)
+
+
+def test_multithreaded_oracle_matches(oracle_lib):
+    for k, E in ((0, 4), (5, 8), (17, 16), (20, 4)):
+        x = pins.fingerprint_elems(1 << k, E, salt=k)
+        for t in (1, 3, 8):
+            got, used = oracle_lib.brev_oop_mt(x, k, E, t)
+            assert used >= 1
+            assert np.array_equal(got, oracle_lib.brev_oop(x, k, E))
+
+
+def test_gather_matches(oracle_lib):
+    k, E = 15, 8
+    x = pins.fingerprint_elems(1 << k, E, salt=1)
+    full = oracle_lib.brev_oop(x, k, E).reshape(-1, E)
+    idx = np.array([0, 1, 7, 1000, (1 << k) - 1, 12345], dtype=np.uint64)
+    got = oracle_lib.brev_gather(x, idx, k, E).reshape(-1, E)
+    assert np.array_equal(got, full[idx.astype(np.int64)])
+
+
+def test_oracle_rejects_bad_args(oracle_lib):
+    L = oracle_lib.lib()
+    assert L.oracle_brev_oop(None, None, 3, 4) == -1
+    buf = np.zeros(64, dtype=np.uint8)
+    assert L.oracle_brev_inplace(buf.ctypes.data, -1, 4) == -1
+    assert L.oracle_brev_inplace(buf.ctypes.data, 3, 0) == -1
+
+
+# ------------------------------------------------------------ mutants --
+def _rev_vec(idx, k):
+    r = np.zeros_like(idx)
+    x = idx.copy()
+    for _ in range(k):
+        r = (r << np.uint64(1)) | (x & np.uint64(1))
+        x = x >> np.uint64(1)
+    return r
+
+
+class _Mutant:
+    """Python copy of the oracle with one planted mistake."""
+
+    def rev_vec(self, idx, k):
+        return _rev_vec(idx, k)
+
+    def rev(self, i, k):
+        return int(self.rev_vec(np.array([i], dtype=np.uint64), k)[0])
+
+    def copy_elem(self, dst, di, src, si, E):
+        dst[di] = src[si]
+
+    def oop(self, src, k, E):
+        n = 1 << k
+        s = np.ascontiguousarray(src).view(np.uint8).reshape(n, E)
+        d = np.zeros_like(s)
+        r = self.rev_vec(np.arange(n, dtype=np.uint64), k).astype(np.int64)
+        self.copy_elem(d, r, s, np.arange(n), E)
+        return d.reshape(-1)
+
+    def inplace(self, buf, k, E):
+        buf[:] = self.oop(buf, k, E)
+        return buf
+
+
+class RotateNotReverse(_Mutant):
+    def rev_vec(self, idx, k):
+        if k == 0:
+            return np.zeros_like(idx)
+        return (idx >> np.uint64(1)) | ((idx & np.uint64(1)) << np.uint64(k - 1))
+
+
+class DroppedLowBit(_Mutant):
+    def rev_vec(self, idx, k):
+        return _rev_vec(idx & ~np.uint64(1), k) | (idx & np.uint64(1) if k else 0)
+
+
+class OffByOneWidth(_Mutant):
+    def rev_vec(self, idx, k):
+        return _rev_vec(idx, k + 1) & np.uint64((1 << k) - 1)
+
+
+class PartialElementCopy(_Mutant):
+    def copy_elem(self, dst, di, src, si, E):
+        dst[di, : max(E - 1, 0)] = src[si, : max(E - 1, 0)]
+
+
+class SwapWithoutComparison(_Mutant):
+    def inplace(self, buf, k, E):
+        n = 1 << k
+        a = buf.reshape(n, E)
+        for i in range(n):
+            r = self.rev(i, k)
+            t = a[i].copy()
+            a[i] = a[r]
+            a[r] = t
+        return buf
+
+
+class HalvesSwapped(_Mutant):
+    """rev(x y) computed as rev(x) rev(y) (operands of the concatenation
+    transposed)."""
+
+    def rev_vec(self, idx, k):
+        h = k // 2
+        lo = idx & np.uint64((1 << h) - 1)
+        hi = idx >> np.uint64(h)
+        return (_rev_vec(hi, k - h) << np.uint64(h)) | _rev_vec(lo, h)
+
+
+@pytest.mark.parametrize("mutant", [RotateNotReverse, DroppedLowBit, OffByOneWidth,
+                                    PartialElementCopy, SwapWithoutComparison,
+                                    HalvesSwapped])
+def test_pins_catch_planted_mistake(mutant):
+    m = mutant()
+    fast = [
+        lambda: pins.check_worked_example(m),
+        lambda: pins.check_brute_force(m, kmax=6),
+        lambda: pins.check_involution(m, ks=range(0, 9), Es=(4, 16)),
+        lambda: pins.check_stockham(m, kmax=6),
+        lambda: pins.check_xor_induction(m, kmax=8),
+        lambda: pins.check_counts(m, kmax=8),
+        lambda: pins.check_classes(m, kmax=6),
+        lambda: pins.check_concatenation(m, trials=300),
+    ]
+    caught = 0
+    for chk in fast:
+        try:
+            chk()
+        except AssertionError:
+            caught += 1
+    assert caught >= 1, f"no pin caught {mutant.__name__}"
