@@ -1,0 +1,556 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 bit-reversed permutation library.
+
+Default workload (one "step"): the single-array sweep
+k = 10..28 x {uint32, float32, complex<float>, complex<double>} x
+{out-of-place, in-place} -- 152 permutations of seeded synthetic arrays,
+34 GiB moved per step.  ``value`` is bit-reverse GB/s counting read + write
+(2 n E bytes per permutation) over the whole step.  The same JSON line also
+carries the batched workload (4096 arrays, k in [8, 20], mixed
+complex<float>/complex<double>: one captured-graph persistent launch vs a
+loop of per-array launches), the roofline of the dominant kernel, the
+end-to-end host-buffer path and the CPU-oracle baseline.
+
+``--impl reference`` times the CPU oracle on the host cores instead (the
+paper has no GPU code to run), on a bounded sample of the same sweep.
+
+Multi-GPU (torchrun, one rank per GPU): every rank runs the same workload on
+its own GPU (replicas; the permutation of one array needs no exchange at
+these sizes), timing takes the max over ranks, value sums all ranks' bytes.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SWEEP_KS = list(range(10, 29))
+SWEEP_KINDS = [("u32", 4), ("f32", 4), ("c64", 8), ("c128", 16)]
+FALLBACK_PEAK_GBS = 6800.0
+
+
+# ------------------------------------------------------------- helpers --
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="brev", choices=["brev", "reference"])
+    ap.add_argument("--kmax", type=int, default=28, help="largest k of the sweep")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_PEAK_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during timed regions."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.samples = []  # (t, sm, max, power, flags)
+        self.windows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        threading.Thread(target=self._read, daemon=True).start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                self.samples.append((time.time(), float(parts[1]), float(parts[2]),
+                                     float(parts[3]) if parts[3] not in ("[N/A]", "") else 0.0,
+                                     parts[5:9]))
+            except ValueError:
+                pass
+
+    def window(self, t0, t1):
+        self.windows.append((t0, t1))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        inside = [s for s in self.samples
+                  if any(a - 0.05 <= s[0] <= b + 0.05 for a, b in self.windows)]
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"],
+                    "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in inside for i, v in enumerate(s[4])
+                          if v.strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(s[1] for s in inside),
+                "sm_max_mhz": max(s[2] for s in inside), "reasons": reasons,
+                "samples": len(inside), "power_w_max": max(s[3] for s in inside)}
+
+
+def shape_name(brev, k, E, inplace):
+    bx, bz = brev.brev_tile_shape(k, E, inplace)
+    if bx == 0:
+        return f"small_E{E}"
+    return f"tile_{'inplace' if inplace else 'oop'}_E{E}_{bx}x{bz}"
+
+
+# ------------------------------------------------------------ the sweep --
+def make_sweep(torch, inputs, kmax, device):
+    pts = []
+    for kind, E in SWEEP_KINDS:
+        for k in range(SWEEP_KS[0], kmax + 1):
+            n = 1 << k
+            src = torch.empty(n * E, dtype=torch.uint8, device=device)
+            inputs.fill_torch(src, 100 + k, kind)
+            dst = torch.empty_like(src)
+            pts.append({"kind": kind, "E": E, "k": k, "src": src, "dst": dst,
+                        "bytes": 2 * n * E})
+    return pts
+
+
+def sweep_order(pts):
+    """All out-of-place launches (ascending k), then all in-place ones: every
+    buffer is touched again only after far more than L2 of other traffic."""
+    seq = [(p, False) for p in pts] + [(p, True) for p in pts]
+    return seq
+
+
+def launch_point(brev, p, inplace, stream):
+    if inplace:
+        brev.lib().brev_permute_to(p["dst"].data_ptr(), p["dst"].data_ptr(), p["k"], p["E"],
+                                   stream)
+    else:
+        brev.lib().brev_permute_to(p["dst"].data_ptr(), p["src"].data_ptr(), p["k"], p["E"],
+                                   stream)
+
+
+def run_brev(args):
+    import torch
+    import torch.distributed as dist
+    from __graft_entry__ import build
+    from paper_1708_01873_gb300 import brev, inputs
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=device)
+    build()
+    info = brev.brev_get_device_info()
+    peak, peak_src = measured_peak()
+    stream = torch.cuda.current_stream(device)
+    sh = stream.cuda_stream
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize(device)
+
+    def max_over_ranks(x):
+        if ws == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    pts = make_sweep(torch, inputs, args.kmax, device)
+    seq = sweep_order(pts)
+    step_bytes = sum(p["bytes"] for p, _ in seq)
+    names = [shape_name(brev, p["k"], p["E"], ip) for p, ip in seq]
+    L = brev.lib()
+    for _ in range(args.warmup):
+        for p, ip in seq:
+            launch_point(brev, p, ip, sh)
+    torch.cuda.synchronize(device)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+
+    # per-launch events inside the timed region (roofline of each kernel)
+    evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in seq] for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    barrier()
+    c0 = L.brev_launch_count()
+    w0 = time.time()
+    t_start.record(stream)
+    for s in range(args.steps):
+        for (p, ip), (ea, eb) in zip(seq, evs[s]):
+            ea.record(stream)
+            launch_point(brev, p, ip, sh)
+            eb.record(stream)
+    t_end.record(stream)
+    barrier()
+    w1 = time.time()
+    sampler.window(w0, w1)
+    launches = L.brev_launch_count() - c0
+    ms_total = max_over_ranks(t_start.elapsed_time(t_end))
+    ms_per_step = ms_total / args.steps
+    value = ws * step_bytes * args.steps / (ms_total * 1e-3) / 1e9
+
+    # per-kernel aggregates from the per-launch events
+    per_kernel = {}
+    per_point = {}
+    for s in range(args.steps):
+        for i, ((p, ip), (ea, eb)) in enumerate(zip(seq, evs[s])):
+            ms = ea.elapsed_time(eb)
+            d = per_kernel.setdefault(names[i], {"ms": 0.0, "bytes": 0, "launches": 0})
+            d["ms"] += ms
+            d["bytes"] += p["bytes"]
+            d["launches"] += 1
+            key = f"{p['kind']}_{'ip' if ip else 'oop'}_k{p['k']}"
+            per_point.setdefault(key, []).append(ms)
+    dom_name = max(per_kernel, key=lambda n: per_kernel[n]["ms"])
+    dom = per_kernel[dom_name]
+    achieved = dom["bytes"] / (dom["ms"] * 1e-3) / 1e9
+    total_kernel_ms = sum(d["ms"] for d in per_kernel.values())
+    traffic = load_traffic(dom_name)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "kernel": dom_name, "peak_source": f"{peak_src} (copy bandwidth)",
+                "share_of_step": round(dom["ms"] / total_kernel_ms, 3),
+                "launches_per_step": dom["launches"] // args.steps,
+                "bytes_per_launch": dom["bytes"] // dom["launches"],
+                "nominal_gbs": round(info["nominal_gbs"], 1),
+                "frac_nominal": round(achieved / info["nominal_gbs"], 4)}
+    large = {}
+    for key, v in per_point.items():
+        k = int(key.rsplit("k", 1)[1])
+        if k >= 26:
+            kind = key.split("_")[0]
+            E = dict(SWEEP_KINDS)[kind]
+            med = statistics.median(v)
+            large[key] = round(2 * (1 << k) * E / (med * 1e-3) / 1e9, 1)
+
+    # ---------------------------------------------------- batched (cfg 4)
+    batched = None
+    if not args.no_batched:
+        batched = bench_batched(torch, brev, inputs, device, stream, sampler, max_over_ranks,
+                                barrier)
+
+    # ------------------------------------------------------------ e2e
+    e2e = None
+    if not args.no_e2e:
+        e2e = bench_e2e(torch, brev, inputs, pts, seq, args.e2e_steps, stream, sampler,
+                        max_over_ranks, barrier, ws)
+    sampler.stop()
+    clocks = sampler.summary()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_baseline(args.cpu_seconds)
+
+    for p in pts:
+        p["src"] = p["dst"] = None
+    if rank == 0:
+        line = {
+            "metric": "bit-reverse GB/s (read+write) & % of HBM peak; batched vs looped launches",
+            "value": round(value, 1), "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u8",
+            "data": "synthetic (seeded SplitMix64: uint32, float32 U[-1,1), complex<float>, "
+                    "complex<double>)",
+            "config": {"workload": "single-array sweep k=10..%d x {uint32, float32, "
+                                   "complex<float>, complex<double>} x {out-of-place, in-place}"
+                                   % args.kmax,
+                       "points_per_step": len(seq), "bytes_per_step": step_bytes,
+                       "l2": "no flush: 34 GiB moved per step, every buffer re-touched only "
+                             "after >= 1 GiB of other traffic (L2 = %d MiB)"
+                             % (info["l2_bytes"] >> 20),
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+            "roofline": roofline,
+            "frac_of_peak": round(value / ws / peak, 4),
+            "frac_of_nominal": round(value / ws / info["nominal_gbs"], 4),
+            "large_arrays_gbs": large,
+            "batched": batched,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+            "device": info["name"],
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def load_traffic(kernel_name):
+    """dram read+write bytes per launch of ``kernel_name`` from the committed
+    ncu summary, if it was taken on the current kernel source."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(p):
+        return None
+    src_hash = hashlib.sha256()
+    for f in ("brev_device.cuh", "brev_kernels.cuh"):
+        with open(os.path.join(ROOT, "paper_1708_01873_gb300", "csrc", f), "rb") as fh:
+            src_hash.update(fh.read())
+    h = src_hash.hexdigest()[:16]
+    with open(p) as fh:
+        for line in fh:
+            parts = line.split()
+            # kernel  source_hash  dram_bytes_per_launch  ...
+            if len(parts) >= 3 and parts[0] == kernel_name and parts[1] == h:
+                try:
+                    return int(float(parts[2]))
+                except ValueError:
+                    return None
+    return None
+
+
+def bench_batched(torch, brev, inputs, device, stream, sampler, max_over_ranks, barrier,
+                  reps=10, warm=3):
+    import numpy as np
+    rng = np.random.default_rng(4)
+    count = 4096
+    ks = rng.integers(8, 21, size=count)
+    Es = rng.choice([8, 16], size=count)
+    arrays = []
+    for i in range(count):
+        E = int(Es[i])
+        a = torch.empty((1 << int(ks[i])) * E, dtype=torch.uint8, device=device)
+        inputs.fill_torch(a, 40000 + i, "c64" if E == 8 else "c128", chunk=1 << 26)
+        arrays.append(a.view(torch.complex64 if E == 8 else torch.complex128))
+    total = sum(2 * a.numel() * a.element_size() for a in arrays)
+    L = brev.lib()
+    sh = stream.cuda_stream
+    plan = brev.BrevPlan(arrays)
+    ptrs = [a.data_ptr() for a in arrays]
+    kk = [int(x) for x in ks]
+    ee = [int(x) for x in Es]
+
+    def loop():
+        for p, k, E in zip(ptrs, kk, ee):
+            L.brev_permute_to(p, p, k, E, sh)
+
+    def one_batched():
+        brev.brev_permute_batched(arrays, stream=stream)
+
+    def graph_replay():
+        plan.launch(stream)
+
+    # the loop of single launches captured into a CUDA graph too
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        for p, k, E in zip(ptrs, kk, ee):
+            L.brev_permute_to(p, p, k, E, torch.cuda.current_stream().cuda_stream)
+
+    def loop_graph():
+        g.replay()
+
+    out = {}
+    for name, fn in (("persistent_graph", graph_replay), ("persistent", one_batched),
+                     ("loop", loop), ("loop_graph", loop_graph)):
+        for _ in range(warm):
+            fn()
+        barrier()
+        ea = torch.cuda.Event(enable_timing=True)
+        eb = torch.cuda.Event(enable_timing=True)
+        w0 = time.time()
+        ea.record(stream)
+        for _ in range(reps):
+            fn()
+        eb.record(stream)
+        barrier()
+        sampler.window(w0, time.time())
+        ms = max_over_ranks(ea.elapsed_time(eb)) / reps
+        out[name] = {"ms": round(ms, 3), "gbs": round(total / (ms * 1e-3) / 1e9, 1)}
+    plan.close()
+    res = {"workload": "4096 arrays, k uniform in [8,20], E uniform in {8,16} (seed 4), "
+                       "in place; persistent = one launch per batch",
+           "bytes_per_batch": total, **out,
+           "speedup_persistent_graph_vs_loop": round(out["loop"]["ms"] /
+                                                     out["persistent_graph"]["ms"], 2),
+           "speedup_persistent_graph_vs_loop_graph": round(out["loop_graph"]["ms"] /
+                                                           out["persistent_graph"]["ms"], 2)}
+    del arrays
+    return res
+
+
+def bench_e2e(torch, brev, inputs, pts, seq, steps, stream, sampler, max_over_ranks, barrier,
+              ws):
+    """The sweep through brev_permute_host: pinned host input copied in,
+    permuted, result copied back, every point every step."""
+    L = brev.lib()
+    sh = stream.cuda_stream
+    kinds = {}
+    for p in pts:
+        kinds[p["kind"]] = max(kinds.get(p["kind"], 0), p["src"].numel())
+    host_src = {}
+    for kind, nbytes in kinds.items():
+        h = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+        # the prefix of a seeded array is the seeded array of that length
+        inputs.fill_torch(h, 100, kind, chunk=1 << 26)
+        host_src[kind] = h
+    host_dst = torch.empty(max(kinds.values()), dtype=torch.uint8, pin_memory=True)
+    h2d = sum(p["src"].numel() for p, _ in seq)
+
+    def step():
+        for p, ip in seq:
+            nb = p["src"].numel()
+            s = host_src[p["kind"]]
+            d = s if ip else host_dst
+            rc = L.brev_permute_host(d.data_ptr(), s.data_ptr(), p["k"], p["E"], sh)
+            if rc != 0:
+                raise RuntimeError(brev.brev_last_error())
+
+    step()  # warm-up (pool growth)
+    # in-place steps change host_src; restore for a clean next run is not
+    # needed for timing (content does not affect the permutation's cost)
+    barrier()
+    w0 = time.time()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    barrier()
+    el = max_over_ranks(time.perf_counter() - t0)
+    sampler.window(w0, time.time())
+    step_bytes = sum(p["bytes"] for p, _ in seq)
+    return {"value": round(ws * step_bytes * steps / el / 1e9, 1), "unit": "GB/s",
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d, "steps": steps,
+            "api": "brev_permute_host (pinned host buffers; H2D + permute + D2H per point)"}
+
+
+# --------------------------------------------------------- CPU baseline --
+def oracle_points(k):
+    from paper_1708_01873_gb300 import inputs
+    return [(kind, E, k, inputs.array_np(100 + k, 1 << k, kind)) for kind, E in SWEEP_KINDS]
+
+
+def time_oracle(points):
+    """Run the plain oracle out-of-place and in-place on every point; returns
+    (algorithmic bytes, seconds spent inside the oracle)."""
+    import oracle
+    nbytes, secs = 0, 0.0
+    for kind, E, k, src in points:
+        t0 = time.perf_counter()
+        oracle.brev_oop(src, k, E)
+        secs += time.perf_counter() - t0
+        b = src.copy()
+        t0 = time.perf_counter()
+        oracle.brev_inplace(b, k, E)
+        secs += time.perf_counter() - t0
+        nbytes += 2 * (2 * (1 << k) * E)
+    return nbytes, secs
+
+
+def largest_k_within(budget_s):
+    """Largest sweep k such that the sweep truncated at k takes about
+    budget_s seconds of oracle time (each k costs about twice the previous)."""
+    import oracle
+    oracle.build()
+    done_s, last_k, pts_all = 0.0, SWEEP_KS[0], []
+    for k in SWEEP_KS:
+        if done_s and done_s * 2.2 > budget_s:
+            break
+        pts = oracle_points(k)
+        _, t = time_oracle(pts)
+        done_s += t
+        last_k = k
+        pts_all += pts
+    return last_k, pts_all
+
+
+def cpu_baseline(budget_s):
+    """The plain single-thread oracle timed on the host cores over the sweep
+    truncated at the largest k that fits about ``budget_s`` seconds."""
+    kmax, pts = largest_k_within(budget_s / 2)
+    nbytes, secs = time_oracle(pts)
+    return {"value": round(nbytes / secs / 1e9, 3), "unit": "GB/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"sweep k=10..{kmax} x {{u32,f32,c64,c128}} x {{oop,in-place}}, "
+                      f"plain single-thread C oracle, {secs:.1f} s timed",
+            "seconds": round(secs, 2)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    # size each step so that the whole run stays within about 90 s
+    budget = max(0.05, 90.0 / max(1, args.steps + args.warmup))
+    kmax, pts = largest_k_within(budget)
+    for _ in range(args.warmup):
+        time_oracle(pts)
+    tot_bytes, secs = 0, 0.0
+    for _ in range(args.steps):
+        b, t = time_oracle(pts)
+        tot_bytes += b
+        secs += t
+    value = tot_bytes / secs / 1e9
+    line = {"metric": "bit-reverse GB/s (read+write) & % of HBM peak; batched vs looped launches",
+            "impl": "reference", "value": round(value, 3), "unit": "GB/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(secs / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic (seeded SplitMix64)",
+            "config": {"workload": f"single-array sweep sample k=10..{kmax} x "
+                                   "{uint32, float32, complex<float>, complex<double>} x "
+                                   "{out-of-place, in-place} (bounded sample of the "
+                                   "k=10..28 sweep)"},
+            "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": 1,
+                             "kind": "oracle",
+                             "sample": f"k=10..{kmax} per step, plain single-thread C oracle"},
+            "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_brev(args)
+
+
+if __name__ == "__main__":
+    main()

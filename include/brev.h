@@ -1,0 +1,189 @@
+/*
+ * brev.h -- C ABI of the GB300 (sm_103a) bit-reversed permutation library.
+ *
+ * The operation (paper: "Practically efficient methods for performing
+ * bit-reversed permutation in C++11 on the x86-64 architecture",
+ * Introduction, definition of the bit-reversed permutation and its n = 8
+ * worked example): for an array of n = 2^k elements, the element at index
+ * i moves to index rev_k(i), the k-bit reversal of i.  Elements are opaque
+ * blobs of elem_bytes bytes (1, 2, 4, 8 or 16: uint8 ... complex<double>);
+ * they are moved, never interpreted, so every bit pattern (NaN, -0.0) is
+ * preserved and results are exact.
+ *
+ * General conventions
+ *   - log2n is k, 0 <= k <= 34; n = 2^k elements.  k = 0 and k = 1 are the
+ *     identity.
+ *   - Data pointers are DEVICE pointers (cudaMalloc / torch CUDA tensors).
+ *     Host or unregistered pointers are rejected with BREV_ERR_INVALID_ARG
+ *     before anything is launched.  Each pointer must be aligned to
+ *     elem_bytes (else BREV_ERR_ALIGNMENT).  Pointers that are also 16-byte
+ *     aligned take the 16-byte vector path; others take an element-wide path
+ *     on the GPU.  There is no CPU fallback.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  All
+ *     calls are stream-ordered and asynchronous: they enqueue work and
+ *     return; the caller synchronises.  Only brev_autotune and
+ *     brev_permute_host (see there) block the calling thread.
+ *   - The caller owns every data buffer.  The library owns only its small
+ *     device workspaces (batch descriptors, host-path staging), plans and
+ *     the tuning table.
+ *   - Every call returns a brev_status.  On failure nothing was enqueued
+ *     (except for BREV_ERR_CUDA raised by the launch itself), and
+ *     brev_last_error() returns a message for the calling thread.
+ *   - Calls are thread-safe.
+ */
+#ifndef BREV_H
+#define BREV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define BREV_API __attribute__((visibility("default")))
+#else
+#define BREV_API
+#endif
+
+#define BREV_VERSION 1000 /* 1.0.0 */
+#define BREV_MAX_LOG2N 34
+
+typedef enum brev_status {
+    BREV_OK = 0,
+    BREV_ERR_INVALID_ARG = 1, /* bad k / elem_bytes / count / null or host pointer */
+    BREV_ERR_ALIGNMENT = 2,   /* pointer not aligned to elem_bytes */
+    BREV_ERR_OVERLAP = 3,     /* out-of-place source and destination partly overlap */
+    BREV_ERR_OOM = 4,         /* a library workspace could not be allocated */
+    BREV_ERR_CUDA = 5,        /* a CUDA runtime call failed (see brev_last_error) */
+    BREV_ERR_UNSUPPORTED = 6  /* a valid request this build does not handle */
+} brev_status;
+
+/* ---------------------------------------------------------------- single */
+
+/* Out-of-place permutation dst[rev_k(i)] = src[i] (Introduction, the
+ * definition; Introduction, "Bit reversal using a matrix buffer": the
+ * kernel is the matrix-buffer method with a 2^bx x 2^bz shared-memory
+ * buffer per tile, index = x y z, destination rev(z) rev(y) rev(x)).
+ * dst and src: device pointers to 2^log2n elements each.  src == dst is
+ * allowed and means in-place (the pair-swap form below).  Partial overlap
+ * returns BREV_ERR_OVERLAP. */
+BREV_API brev_status brev_permute_to(void *dst, const void *src, int log2n, int elem_bytes,
+                            void *stream);
+
+/* Single-pointer form.  in_place != 0: `data` holds 2^log2n elements and is
+ * permuted in place (Introduction, Listing 1: each index swaps with its
+ * reverse once; here each tile swaps with its partner tile rev(y), and
+ * self-paired tiles are permuted inside one CTA).  in_place == 0: `data`
+ * holds 2n elements laid out as [src | dst]; the first n are read and the
+ * permutation is written to the second n. */
+BREV_API brev_status brev_permute(void *data, int log2n, int elem_bytes, int in_place,
+                         void *stream);
+
+/* ---------------------------------------------------------------- batched */
+
+/* In-place permutation of `count` independent arrays in ONE persistent
+ * kernel launch (a work queue over tiles; no counterpart in the paper,
+ * whose methods handle one array).  ptr_array[i] is a device pointer to
+ * 2^log2n_array[i] elements of elem_bytes bytes.  ptr_array and
+ * log2n_array are HOST arrays, read before the call returns.  Arrays must
+ * not overlap one another.  count == 0 is a no-op. */
+BREV_API brev_status brev_permute_batched(void *const *ptr_array, const int *log2n_array,
+                                 int count, int elem_bytes, void *stream);
+
+/* The same with a per-array element size (mixed complex<float> and
+ * complex<double> batches in one launch).  elem_bytes_array is a host
+ * array of count entries, each in {1,2,4,8,16}. */
+BREV_API brev_status brev_permute_batched_mixed(void *const *ptr_array, const int *log2n_array,
+                                       const int *elem_bytes_array, int count,
+                                       void *stream);
+
+/* A batch captured once into a CUDA graph (ticket reset + persistent
+ * kernel) and replayed by brev_plan_launch.  The arrays' pointers and
+ * sizes are fixed at creation; their contents may change between
+ * launches.  Each launch permutes every array in place once (so two
+ * launches restore the input).  elem_bytes_array may be NULL with
+ * elem_bytes giving one size for all arrays.  Creation allocates the
+ * plan's device workspace and may synchronise the device. */
+typedef struct brev_plan brev_plan;
+BREV_API brev_status brev_plan_create(void *const *ptr_array, const int *log2n_array,
+                             const int *elem_bytes_array, int elem_bytes, int count,
+                             brev_plan **out_plan);
+BREV_API brev_status brev_plan_launch(brev_plan *plan, void *stream);
+BREV_API void brev_plan_destroy(brev_plan *plan);
+
+/* ---------------------------------------------------------------- host path */
+
+/* End-to-end form for host buffers: copies src_host (2^log2n elements) to
+ * a library-owned device workspace, permutes, and copies the result to
+ * dst_host (which may equal src_host), all on `stream`, then waits for
+ * the stream.  Pinned host memory gives the full link bandwidth; pageable
+ * memory works but is slower.  The workspace is stream-ordered device
+ * memory released back to the pool at the end of the call. */
+BREV_API brev_status brev_permute_host(void *dst_host, const void *src_host, int log2n,
+                              int elem_bytes, void *stream);
+
+/* ---------------------------------------------------------------- tuning */
+
+/* Tile shape used for (log2n, elem_bytes, in_place): bx high bits and bz
+ * low bits per tile (the matrix-buffer side lengths 2^bx, 2^bz); bx = bz =
+ * 0 means the whole array is staged in one CTA (small arrays).  Host-only
+ * query, no GPU needed. */
+BREV_API brev_status brev_tile_shape(int log2n, int elem_bytes, int in_place, int *bx, int *bz);
+
+/* Run the permutation with a forced tile shape (tests and the tuner).
+ * Out-of-place accepts bx != bz; in-place requires bx == bz.  Shapes that
+ * are not compiled in return BREV_ERR_UNSUPPORTED.  src == dst means
+ * in-place. */
+BREV_API brev_status brev_permute_shape(void *dst, const void *src, int log2n, int elem_bytes,
+                               int bx, int bz, void *stream);
+
+/* Number of compiled 16-byte-path tile shapes for (elem_bytes, in_place),
+ * and the i-th one (host-only; the tuner's candidates). */
+BREV_API int brev_shape_count(int elem_bytes, int in_place);
+BREV_API brev_status brev_shape_at(int elem_bytes, int in_place, int i, int *bx, int *bz);
+
+/* Time every compiled shape for k in [k_min, k_max] (out-of-place and
+ * in-place), keep the fastest in the library's table, and, if cache_path
+ * is not NULL, write the table as JSON.  Allocates and frees its own
+ * device buffers; blocks the calling thread. */
+BREV_API brev_status brev_autotune(int k_min, int k_max, int elem_bytes, const char *cache_path);
+
+/* Load a table written by brev_autotune.  Entries whose device name or SM
+ * count differ from the current device are ignored.  Host-only apart from
+ * the device-name query. */
+BREV_API brev_status brev_load_tune_cache(const char *cache_path);
+
+/* Forget tuned shapes (back to the built-in defaults). */
+BREV_API void brev_reset_tuning(void);
+
+/* ---------------------------------------------------------------- info */
+
+typedef struct brev_device_info {
+    int sm_count;
+    int l2_bytes;
+    int mem_clock_khz;   /* peak memory clock */
+    int mem_bus_bits;    /* global memory bus width */
+    double nominal_gbs;  /* mem_clock_khz * 2 (DDR) * mem_bus_bits / 8 */
+    int max_smem_per_block;
+    char name[96];
+} brev_device_info;
+
+/* Properties of the current device (needs a GPU). */
+BREV_API brev_status brev_get_device_info(brev_device_info *out);
+
+/* Number of kernel launches the library has issued on this process (all
+ * entry points); lets callers count launches inside a timed region. */
+BREV_API uint64_t brev_launch_count(void);
+
+BREV_API const char *brev_status_string(brev_status s);
+/* Message of the last failing call on this thread ("" if none). */
+BREV_API const char *brev_last_error(void);
+BREV_API int brev_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BREV_H */

@@ -1,0 +1,274 @@
+"""Python binding of the C ABI in ``include/brev.h`` (ctypes).
+
+Argument marshalling only: every permutation runs in the CUDA kernels of
+``libbrev.so``.  Functions carry the C names; they take torch tensors (any
+dtype -- the element size is ``tensor.element_size()``; elements are moved
+as opaque bytes), infer log2n from the element count, pass the current
+torch CUDA stream unless one is given, and raise :class:`BrevError` when the
+library returns a non-OK status.  There is no CPU fallback: if the library
+is missing, :func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Iterable, Sequence
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbrev.so")
+
+BREV_OK = 0
+STATUS_NAMES = {0: "BREV_OK", 1: "BREV_ERR_INVALID_ARG", 2: "BREV_ERR_ALIGNMENT",
+                3: "BREV_ERR_OVERLAP", 4: "BREV_ERR_OOM", 5: "BREV_ERR_CUDA",
+                6: "BREV_ERR_UNSUPPORTED"}
+
+# symbol name -> (restype, argtypes)
+_vp, _i, _u64, _cp = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_char_p
+_ip = ctypes.POINTER(ctypes.c_int)
+_vpp = ctypes.POINTER(ctypes.c_void_p)
+
+
+class DeviceInfo(ctypes.Structure):
+    _fields_ = [("sm_count", ctypes.c_int), ("l2_bytes", ctypes.c_int),
+                ("mem_clock_khz", ctypes.c_int), ("mem_bus_bits", ctypes.c_int),
+                ("nominal_gbs", ctypes.c_double), ("max_smem_per_block", ctypes.c_int),
+                ("name", ctypes.c_char * 96)]
+
+
+SIGNATURES = {
+    "brev_permute_to": (_i, [_vp, _vp, _i, _i, _vp]),
+    "brev_permute": (_i, [_vp, _i, _i, _i, _vp]),
+    "brev_permute_batched": (_i, [_vpp, _ip, _i, _i, _vp]),
+    "brev_permute_batched_mixed": (_i, [_vpp, _ip, _ip, _i, _vp]),
+    "brev_plan_create": (_i, [_vpp, _ip, _ip, _i, _i, ctypes.POINTER(_vp)]),
+    "brev_plan_launch": (_i, [_vp, _vp]),
+    "brev_plan_destroy": (None, [_vp]),
+    "brev_permute_host": (_i, [_vp, _vp, _i, _i, _vp]),
+    "brev_tile_shape": (_i, [_i, _i, _i, _ip, _ip]),
+    "brev_permute_shape": (_i, [_vp, _vp, _i, _i, _i, _i, _vp]),
+    "brev_shape_count": (_i, [_i, _i]),
+    "brev_shape_at": (_i, [_i, _i, _i, _ip, _ip]),
+    "brev_autotune": (_i, [_i, _i, _i, _cp]),
+    "brev_load_tune_cache": (_i, [_cp]),
+    "brev_reset_tuning": (None, []),
+    "brev_get_device_info": (_i, [ctypes.POINTER(DeviceInfo)]),
+    "brev_launch_count": (_u64, []),
+    "brev_status_string": (_cp, [_i]),
+    "brev_last_error": (_cp, []),
+    "brev_version": (_i, []),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class BrevError(RuntimeError):
+    def __init__(self, status: int, func: str, message: str):
+        self.status = status
+        self.status_name = STATUS_NAMES.get(status, str(status))
+        super().__init__(f"{func}: {self.status_name}: {message}")
+
+
+def lib() -> ctypes.CDLL:
+    """Load libbrev.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(
+                    f"{LIB_PATH} is missing: build it with "
+                    "paper_1708_01873_gb300.build.build_library() (needs nvcc)")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(status: int, func: str) -> None:
+    if status != BREV_OK:
+        msg = lib().brev_last_error().decode(errors="replace")
+        raise BrevError(status, func, msg)
+
+
+def _log2(n: int) -> int:
+    if n <= 0 or n & (n - 1):
+        raise ValueError(f"element count {n} is not a power of two")
+    return n.bit_length() - 1
+
+
+def _stream_handle(stream, device=None) -> int:
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream(device).cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _flat(t):
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t
+
+
+# ------------------------------------------------------------ single --
+def brev_permute_to(dst, src, stream=None) -> None:
+    """dst[rev(i)] = src[i] (src may be dst: in place)."""
+    _flat(dst), _flat(src)
+    if dst.element_size() != src.element_size() or dst.numel() != src.numel():
+        raise ValueError("dst and src must have the same element size and count")
+    k = _log2(src.numel())
+    _check(lib().brev_permute_to(dst.data_ptr(), src.data_ptr(), k, src.element_size(),
+                                 _stream_handle(stream, src.device)), "brev_permute_to")
+
+
+def brev_permute(data, in_place: bool = True, stream=None) -> None:
+    """in_place: permute ``data`` (2^k elements).  Otherwise ``data`` holds
+    [src | dst] (2 * 2^k elements) and the result goes to its second half."""
+    _flat(data)
+    n = data.numel() if in_place else data.numel() // 2
+    if not in_place and data.numel() % 2:
+        raise ValueError("[src | dst] buffer needs an even element count")
+    k = _log2(n)
+    _check(lib().brev_permute(data.data_ptr(), k, data.element_size(), int(bool(in_place)),
+                              _stream_handle(stream, data.device)), "brev_permute")
+
+
+def brev_permute_shape(dst, src, bx: int, bz: int, stream=None) -> None:
+    """Forced tile shape (2^bx x 2^bz; 0, 0 = whole array in one CTA)."""
+    _flat(dst), _flat(src)
+    k = _log2(src.numel())
+    _check(lib().brev_permute_shape(dst.data_ptr(), src.data_ptr(), k, src.element_size(),
+                                    bx, bz, _stream_handle(stream, src.device)),
+           "brev_permute_shape")
+
+
+# ----------------------------------------------------------- batched --
+def _batch_arrays(tensors: Sequence):
+    n = len(tensors)
+    ptrs = (ctypes.c_void_p * max(n, 1))()
+    ks = (ctypes.c_int * max(n, 1))()
+    es = (ctypes.c_int * max(n, 1))()
+    for i, t in enumerate(tensors):
+        _flat(t)
+        ptrs[i] = t.data_ptr()
+        ks[i] = _log2(t.numel())
+        es[i] = t.element_size()
+    return ptrs, ks, es
+
+
+def brev_permute_batched(tensors: Sequence, stream=None) -> None:
+    """Permute every tensor in place in one persistent launch (tensors may
+    have different element sizes and lengths)."""
+    tensors = list(tensors)
+    if not tensors:
+        return
+    ptrs, ks, es = _batch_arrays(tensors)
+    _check(lib().brev_permute_batched_mixed(ptrs, ks, es, len(tensors),
+                                            _stream_handle(stream, tensors[0].device)),
+           "brev_permute_batched_mixed")
+
+
+brev_permute_batched_mixed = brev_permute_batched
+
+
+class BrevPlan:
+    """A captured batch (brev_plan_create); ``launch`` replays it."""
+
+    def __init__(self, tensors: Iterable):
+        self.tensors = list(tensors)  # keeps the storage alive
+        ptrs, ks, es = _batch_arrays(self.tensors)
+        h = ctypes.c_void_p()
+        _check(lib().brev_plan_create(ptrs, ks, es, 0, len(self.tensors), ctypes.byref(h)),
+               "brev_plan_create")
+        self._h = h
+
+    def launch(self, stream=None) -> None:
+        dev = self.tensors[0].device if self.tensors else None
+        _check(lib().brev_plan_launch(self._h, _stream_handle(stream, dev)), "brev_plan_launch")
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) and self._h.value:
+            lib().brev_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def brev_plan_create(tensors: Iterable) -> BrevPlan:
+    return BrevPlan(tensors)
+
+
+# -------------------------------------------------------------- host --
+def brev_permute_host(dst, src, stream=None) -> None:
+    """Host (CPU, ideally pinned) tensors: copy in, permute on the GPU, copy
+    out; returns when the result is in ``dst``."""
+    _flat(dst), _flat(src)
+    k = _log2(src.numel())
+    import torch
+    s = _stream_handle(stream, torch.device("cuda", torch.cuda.current_device()))
+    _check(lib().brev_permute_host(dst.data_ptr(), src.data_ptr(), k, src.element_size(), s),
+           "brev_permute_host")
+
+
+# ------------------------------------------------------------ tuning --
+def brev_tile_shape(log2n: int, elem_bytes: int, in_place: bool) -> tuple[int, int]:
+    bx, bz = ctypes.c_int(), ctypes.c_int()
+    _check(lib().brev_tile_shape(log2n, elem_bytes, int(bool(in_place)), ctypes.byref(bx),
+                                 ctypes.byref(bz)), "brev_tile_shape")
+    return bx.value, bz.value
+
+
+def brev_shapes(elem_bytes: int, in_place: bool) -> list[tuple[int, int]]:
+    out = []
+    for i in range(lib().brev_shape_count(elem_bytes, int(bool(in_place)))):
+        bx, bz = ctypes.c_int(), ctypes.c_int()
+        _check(lib().brev_shape_at(elem_bytes, int(bool(in_place)), i, ctypes.byref(bx),
+                                   ctypes.byref(bz)), "brev_shape_at")
+        out.append((bx.value, bz.value))
+    return out
+
+
+def brev_autotune(k_min: int, k_max: int, elem_bytes: int, cache_path: str | None) -> None:
+    p = cache_path.encode() if cache_path else None
+    _check(lib().brev_autotune(k_min, k_max, elem_bytes, p), "brev_autotune")
+
+
+def brev_load_tune_cache(path: str) -> None:
+    _check(lib().brev_load_tune_cache(path.encode()), "brev_load_tune_cache")
+
+
+def brev_reset_tuning() -> None:
+    lib().brev_reset_tuning()
+
+
+def brev_get_device_info() -> dict:
+    info = DeviceInfo()
+    _check(lib().brev_get_device_info(ctypes.byref(info)), "brev_get_device_info")
+    return {"name": info.name.decode(), "sm_count": info.sm_count, "l2_bytes": info.l2_bytes,
+            "mem_clock_khz": info.mem_clock_khz, "mem_bus_bits": info.mem_bus_bits,
+            "nominal_gbs": info.nominal_gbs, "max_smem_per_block": info.max_smem_per_block}
+
+
+def brev_launch_count() -> int:
+    return int(lib().brev_launch_count())
+
+
+def brev_status_string(status: int) -> str:
+    return lib().brev_status_string(status).decode()
+
+
+def brev_last_error() -> str:
+    return lib().brev_last_error().decode(errors="replace")
+
+
+def brev_version() -> int:
+    return int(lib().brev_version())

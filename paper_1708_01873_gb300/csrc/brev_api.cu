@@ -1,0 +1,694 @@
+// C ABI of the library: argument checks, tile-shape choice (built-in
+// defaults or a tuned table), single-array launches, the host-buffer path,
+// the autotuner and its JSON cache, device queries and error reporting.
+#include <algorithm>
+#include <atomic>
+#include <cerrno>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <set>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "brev_device.cuh"
+#include "brev_internal.h"
+
+namespace brev {
+
+// ------------------------------------------------------------- errors --
+static thread_local std::string t_last_error;
+static std::atomic<uint64_t> g_launches{0};
+
+void note_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void note_launch_adjust(int64_t delta) {
+  g_launches.fetch_add((uint64_t)delta, std::memory_order_relaxed);
+}
+
+brev_status set_error(brev_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  t_last_error = buf;
+  return s;
+}
+
+brev_status cuda_error(cudaError_t e, const char* what) {
+  cudaGetLastError();  // clear a sticky-free launch error so the next call starts clean
+  return set_error(BREV_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+static bool valid_E(int E) { return E == 1 || E == 2 || E == 4 || E == 8 || E == 16; }
+static int e_index(int E) {
+  switch (E) {
+    case 16: return 0;
+    case 8: return 1;
+    case 4: return 2;
+    case 2: return 3;
+    case 1: return 4;
+  }
+  return -1;
+}
+
+// ------------------------------------------------------- device state --
+static std::mutex g_mu;
+static std::set<std::pair<const void*, int>> g_smem_done;
+
+cudaError_t ensure_smem(const void* kernel, unsigned smem) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (g_smem_done.count({kernel, dev})) return cudaSuccess;
+  // the largest size any launch of this kernel may ask for
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) {
+    // raise to the device maximum once so later, larger requests need no update
+    int mx = 0;
+    cudaFuncAttributes fa;
+    if (cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+        cudaFuncGetAttributes(&fa, kernel) == cudaSuccess) {
+      mx -= (int)fa.sharedSizeBytes;
+      if (mx >= (int)smem &&
+          cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) ==
+              cudaSuccess)
+        g_smem_done.insert({kernel, dev});
+    }
+    cudaGetLastError();
+  }
+  return e;
+}
+
+int current_device_sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+    cudaGetLastError();
+    return 1;
+  }
+  return n;
+}
+
+// cuMemGetAddressRange through the runtime's driver entry-point query, so
+// the library needs no link-time dependency on the driver library.
+typedef int (*AddrRangeFn)(unsigned long long* base, size_t* size, unsigned long long ptr);
+static AddrRangeFn address_range_fn() {
+  static AddrRangeFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (AddrRangeFn)p;
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+brev_status check_device_range(const void* p, uint64_t bytes, const char* what) {
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(BREV_ERR_INVALID_ARG, "%s (%p) is not known to CUDA: %s", what, p,
+                     cudaGetErrorString(e));
+  }
+  if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+    return set_error(BREV_ERR_INVALID_ARG, "%s (%p) is not device memory", what, p);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (a.type == cudaMemoryTypeDevice && a.device != dev)
+    return set_error(BREV_ERR_INVALID_ARG, "%s (%p) belongs to device %d, current device is %d",
+                     what, p, a.device, dev);
+  if (AddrRangeFn fn = address_range_fn()) {
+    unsigned long long base = 0;
+    size_t size = 0;
+    if (fn(&base, &size, (unsigned long long)(uintptr_t)p) == 0) {
+      const unsigned long long lo = (unsigned long long)(uintptr_t)p;
+      if (lo + bytes > base + size)
+        return set_error(BREV_ERR_INVALID_ARG,
+                         "%s: %llu bytes at %p run past the end of its allocation "
+                         "(%zu bytes at 0x%llx)",
+                         what, (unsigned long long)bytes, p, size, base);
+    }
+  }
+  return BREV_OK;
+}
+
+// -------------------------------------------------------- shape table --
+static const ShapeEntry* table_for(int E, int* n) {
+  switch (E) {
+    case 16: *n = g_shapes_e16_n; return g_shapes_e16;
+    case 8: *n = g_shapes_e8_n; return g_shapes_e8;
+    case 4: *n = g_shapes_e4_n; return g_shapes_e4;
+    case 2:
+    case 1: *n = g_shapes_e21_n; return g_shapes_e21;
+  }
+  *n = 0;
+  return nullptr;
+}
+
+static const ShapeEntry* find_shape(int E, int W, int bx, int bz, int kind) {
+  int n = 0;
+  const ShapeEntry* t = table_for(E, &n);
+  for (int i = 0; i < n; ++i)
+    if (t[i].E == E && t[i].W == W && t[i].bx == bx && t[i].bz == bz && t[i].kind == kind)
+      return &t[i];
+  return nullptr;
+}
+
+// Built-in square tile exponents: tiles of 8-32 KiB whose rows are
+// 256-512 bytes, chosen before any tuning.
+static int default_b(int E, bool inplace) {
+  switch (E) {
+    case 16: return 5;              // 512 B rows, 16 KiB tile
+    case 8: return inplace ? 5 : 6;  // 256 B / 512 B rows
+    case 4: return 6;               // 256 B rows, 16 KiB tile
+    case 2: return 7;
+    case 1: return 8;
+  }
+  return 0;
+}
+
+// tuned (bx, bz) per element size, in-place flag and k; 0 = not tuned
+static int8_t g_tuned[5][2][BREV_MAX_LOG2N + 1][2];
+static double g_tuned_gbs[5][2][BREV_MAX_LOG2N + 1];
+
+struct Choice {
+  bool small;
+  const ShapeEntry* entry;
+};
+
+static Choice choose(int k, int E, bool inplace, bool vec16) {
+  const int bmin = b_min_for(E);
+  if (k < 2 * bmin) return {true, nullptr};
+  const int kind = inplace ? 1 : 0;
+  if (vec16) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    const int8_t* t = g_tuned[e_index(E)][kind][k];
+    if (t[0] > 0 && t[1] > 0 && t[0] + t[1] <= k)
+      if (const ShapeEntry* s = find_shape(E, 16, t[0], t[1], kind)) return {false, s};
+  }
+  const int W = vec16 ? 16 : E;
+  for (int b = std::min(default_b(E, inplace), k / 2); b >= bmin; --b)
+    if (const ShapeEntry* s = find_shape(E, W, b, b, kind)) return {false, s};
+  // element-wide path compiles only the narrowest shapes
+  for (int b = bmin; 2 * b <= k; ++b)
+    if (const ShapeEntry* s = find_shape(E, W, b, b, kind)) return {false, s};
+  return {false, nullptr};
+}
+
+static brev_status launch_choice(const Choice& c, void* dst, const void* src, int k, int E,
+                                 cudaStream_t stream) {
+  cudaError_t e;
+  if (c.small) {
+    const void* kern = small_kernel(E);
+    const unsigned smem = (unsigned)E << k;
+    char* d = (char*)dst;
+    const char* s = (const char*)src;
+    void* args[] = {(void*)&d, (void*)&s, (void*)&k};
+    e = cudaLaunchKernel(kern, dim3(1), dim3(256), args, smem, stream);
+    if (e != cudaSuccess) return cuda_error(e, "small-array kernel launch");
+    note_launch();
+    return BREV_OK;
+  }
+  const ShapeEntry* t = c.entry;
+  if (!t) return set_error(BREV_ERR_UNSUPPORTED, "no compiled tile shape for k=%d E=%d", k, E);
+  e = ensure_smem(t->kernel, t->smem);
+  if (e != cudaSuccess) return cuda_error(e, "shared-memory limit");
+  if (t->kind == 0) {
+    const unsigned long long grid = 1ull << (k - t->bx - t->bz);
+    char* d = (char*)dst;
+    const char* s = (const char*)src;
+    void* args[] = {(void*)&d, (void*)&s, (void*)&k};
+    e = cudaLaunchKernel(t->kernel, dim3((unsigned)grid), dim3(t->threads), args, t->smem,
+                         stream);
+  } else {
+    const int w = k - 2 * t->bx;
+    const unsigned long long grid = (unsigned long long)count_lt(w) + count_self(w);
+    char* d = (char*)dst;
+    void* args[] = {(void*)&d, (void*)&k};
+    e = cudaLaunchKernel(t->kernel, dim3((unsigned)grid), dim3(t->threads), args, t->smem,
+                         stream);
+  }
+  if (e != cudaSuccess) return cuda_error(e, "tile kernel launch");
+  note_launch();
+  return BREV_OK;
+}
+
+brev_status launch_single(void* dst, const void* src, int k, int E, cudaStream_t stream) {
+  const bool inplace = dst == src;
+  if (inplace && k <= 1) return BREV_OK;  // identity
+  const bool vec16 = (((uintptr_t)dst | (uintptr_t)src) % 16) == 0;
+  return launch_choice(choose(k, E, inplace, vec16), dst, src, k, E, stream);
+}
+
+static brev_status check_common(int k, int E) {
+  if (!valid_E(E))
+    return set_error(BREV_ERR_INVALID_ARG, "elem_bytes=%d (must be 1, 2, 4, 8 or 16)", E);
+  if (k < 0 || k > BREV_MAX_LOG2N)
+    return set_error(BREV_ERR_INVALID_ARG, "log2n=%d outside [0, %d]", k, BREV_MAX_LOG2N);
+  return BREV_OK;
+}
+
+static brev_status check_pair(void* dst, const void* src, int k, int E) {
+  brev_status s = check_common(k, E);
+  if (s != BREV_OK) return s;
+  if (!dst || !src) return set_error(BREV_ERR_INVALID_ARG, "NULL data pointer");
+  if ((uintptr_t)dst % E || (uintptr_t)src % E)
+    return set_error(BREV_ERR_ALIGNMENT, "pointers must be aligned to elem_bytes=%d", E);
+  const uint64_t bytes = (uint64_t)E << k;
+  if (dst != src) {
+    const uint64_t d = (uintptr_t)dst, sr = (uintptr_t)src;
+    if (d < sr + bytes && sr < d + bytes)
+      return set_error(BREV_ERR_OVERLAP, "source and destination overlap partially");
+  }
+  s = check_device_range(src, bytes, "source");
+  if (s != BREV_OK) return s;
+  if (dst != src) s = check_device_range(dst, bytes, "destination");
+  return s;
+}
+
+brev_status validate_batch_items(const BatchItem* items, int count) {
+  std::vector<std::pair<uint64_t, uint64_t>> ranges;
+  ranges.reserve(count);
+  for (int i = 0; i < count; ++i) {
+    const BatchItem& it = items[i];
+    brev_status s = check_common(it.k, it.E);
+    if (s != BREV_OK) return set_error(s, "array %d: %s", i, t_last_error.c_str());
+    if (!it.ptr) return set_error(BREV_ERR_INVALID_ARG, "array %d: NULL pointer", i);
+    if ((uintptr_t)it.ptr % it.E)
+      return set_error(BREV_ERR_ALIGNMENT, "array %d: pointer not aligned to %d bytes", i, it.E);
+    const uint64_t bytes = (uint64_t)it.E << it.k;
+    s = check_device_range(it.ptr, bytes, "array");
+    if (s != BREV_OK) return set_error(s, "array %d: %s", i, t_last_error.c_str());
+    ranges.push_back({(uint64_t)(uintptr_t)it.ptr, bytes});
+  }
+  std::sort(ranges.begin(), ranges.end());
+  for (size_t i = 1; i < ranges.size(); ++i)
+    if (ranges[i - 1].first + ranges[i - 1].second > ranges[i].first)
+      return set_error(BREV_ERR_OVERLAP, "two arrays of the batch overlap");
+  return BREV_OK;
+}
+
+}  // namespace brev
+
+using namespace brev;
+
+// ================================================================ C ABI ==
+extern "C" {
+
+brev_status brev_permute_to(void* dst, const void* src, int log2n, int elem_bytes, void* stream) {
+  brev_status s = check_pair(dst, src, log2n, elem_bytes);
+  if (s != BREV_OK) return s;
+  return launch_single(dst, src, log2n, elem_bytes, (cudaStream_t)stream);
+}
+
+brev_status brev_permute(void* data, int log2n, int elem_bytes, int in_place, void* stream) {
+  brev_status s = check_common(log2n, elem_bytes);
+  if (s != BREV_OK) return s;
+  if (!data) return set_error(BREV_ERR_INVALID_ARG, "NULL data pointer");
+  if (in_place) return brev_permute_to(data, data, log2n, elem_bytes, stream);
+  char* src = (char*)data;
+  s = check_device_range(data, 2 * ((uint64_t)elem_bytes << log2n), "data ([src | dst])");
+  if (s != BREV_OK) return s;
+  return brev_permute_to(src + ((size_t)elem_bytes << log2n), src, log2n, elem_bytes, stream);
+}
+
+brev_status brev_permute_shape(void* dst, const void* src, int log2n, int elem_bytes, int bx,
+                               int bz, void* stream) {
+  brev_status s = check_pair(dst, src, log2n, elem_bytes);
+  if (s != BREV_OK) return s;
+  const bool inplace = dst == src;
+  const bool vec16 = (((uintptr_t)dst | (uintptr_t)src) % 16) == 0;
+  Choice c{false, nullptr};
+  if (bx == 0 && bz == 0) {
+    if (log2n >= 2 * b_min_for(elem_bytes))
+      return set_error(BREV_ERR_UNSUPPORTED, "whole-array staging only for k < %d",
+                       2 * b_min_for(elem_bytes));
+    c.small = true;
+  } else {
+    if (bx < 0 || bz < 0 || bx + bz > log2n)
+      return set_error(BREV_ERR_INVALID_ARG, "tile %dx%d does not fit k=%d", bx, bz, log2n);
+    if (inplace && bx != bz)
+      return set_error(BREV_ERR_INVALID_ARG, "in-place needs a square tile");
+    c.entry = find_shape(elem_bytes, vec16 ? 16 : elem_bytes, bx, bz, inplace ? 1 : 0);
+    if (!c.entry)
+      return set_error(BREV_ERR_UNSUPPORTED, "tile %dx%d not compiled for E=%d (%s path)", bx, bz,
+                       elem_bytes, vec16 ? "16-byte" : "element-wide");
+  }
+  if (inplace && log2n <= 1) return BREV_OK;
+  return launch_choice(c, dst, src, log2n, elem_bytes, (cudaStream_t)stream);
+}
+
+brev_status brev_permute_batched_mixed(void* const* ptr_array, const int* log2n_array,
+                                       const int* elem_bytes_array, int count, void* stream) {
+  if (count < 0) return set_error(BREV_ERR_INVALID_ARG, "count=%d", count);
+  if (count == 0) return BREV_OK;
+  if (!ptr_array || !log2n_array || !elem_bytes_array)
+    return set_error(BREV_ERR_INVALID_ARG, "NULL host array");
+  std::vector<BatchItem> items(count);
+  for (int i = 0; i < count; ++i)
+    items[i] = BatchItem{ptr_array[i], log2n_array[i], elem_bytes_array[i]};
+  brev_status s = validate_batch_items(items.data(), count);
+  if (s != BREV_OK) return s;
+  return batched_launch(items.data(), count, (cudaStream_t)stream);
+}
+
+brev_status brev_permute_batched(void* const* ptr_array, const int* log2n_array, int count,
+                                 int elem_bytes, void* stream) {
+  if (count < 0) return set_error(BREV_ERR_INVALID_ARG, "count=%d", count);
+  if (count == 0) return BREV_OK;
+  std::vector<int> es(count, elem_bytes);
+  return brev_permute_batched_mixed(ptr_array, log2n_array, es.data(), count, stream);
+}
+
+brev_status brev_permute_host(void* dst_host, const void* src_host, int log2n, int elem_bytes,
+                              void* stream) {
+  brev_status s = check_common(log2n, elem_bytes);
+  if (s != BREV_OK) return s;
+  if (!dst_host || !src_host) return set_error(BREV_ERR_INVALID_ARG, "NULL host pointer");
+  for (const void* p : {(const void*)dst_host, src_host}) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(BREV_ERR_INVALID_ARG, "host pointer %p is not usable", p);
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)
+      return set_error(BREV_ERR_INVALID_ARG, "%p is device memory; use brev_permute_to", p);
+  }
+  const uint64_t bytes = (uint64_t)elem_bytes << log2n;
+  if (dst_host != src_host) {
+    const uint64_t d = (uintptr_t)dst_host, sr = (uintptr_t)src_host;
+    if (d < sr + bytes && sr < d + bytes)
+      return set_error(BREV_ERR_OVERLAP, "host source and destination overlap partially");
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  void* buf = nullptr;
+  cudaError_t e = cudaMallocAsync(&buf, bytes, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(BREV_ERR_OOM, "device workspace of %llu bytes: %s",
+                     (unsigned long long)bytes, cudaGetErrorString(e));
+  }
+  e = cudaMemcpyAsync(buf, src_host, bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    s = launch_single(buf, buf, log2n, elem_bytes, st);
+    if (s == BREV_OK) {
+      e = cudaMemcpyAsync(dst_host, buf, bytes, cudaMemcpyDeviceToHost, st);
+    }
+  }
+  cudaFreeAsync(buf, st);
+  if (e != cudaSuccess) return cuda_error(e, "host-path copy");
+  if (s != BREV_OK) return s;
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_error(e, "host-path synchronize");
+  return BREV_OK;
+}
+
+brev_status brev_tile_shape(int log2n, int elem_bytes, int in_place, int* bx, int* bz) {
+  brev_status s = check_common(log2n, elem_bytes);
+  if (s != BREV_OK) return s;
+  if (!bx || !bz) return set_error(BREV_ERR_INVALID_ARG, "NULL output");
+  Choice c = choose(log2n, elem_bytes, in_place != 0, true);
+  if (c.small) {
+    *bx = *bz = 0;
+    return BREV_OK;
+  }
+  if (!c.entry) return set_error(BREV_ERR_UNSUPPORTED, "no tile shape");
+  *bx = c.entry->bx;
+  *bz = c.entry->bz;
+  return BREV_OK;
+}
+
+int brev_shape_count(int elem_bytes, int in_place) {
+  int n = 0, c = 0;
+  const ShapeEntry* t = table_for(elem_bytes, &n);
+  const int kind = in_place ? 1 : 0;
+  for (int i = 0; i < n; ++i)
+    if (t[i].E == elem_bytes && t[i].W == 16 && t[i].kind == kind) ++c;
+  return c;
+}
+
+brev_status brev_shape_at(int elem_bytes, int in_place, int i, int* bx, int* bz) {
+  int n = 0, c = 0;
+  const ShapeEntry* t = table_for(elem_bytes, &n);
+  const int kind = in_place ? 1 : 0;
+  if (!bx || !bz) return set_error(BREV_ERR_INVALID_ARG, "NULL output");
+  for (int j = 0; j < n; ++j)
+    if (t[j].E == elem_bytes && t[j].W == 16 && t[j].kind == kind) {
+      if (c == i) {
+        *bx = t[j].bx;
+        *bz = t[j].bz;
+        return BREV_OK;
+      }
+      ++c;
+    }
+  return set_error(BREV_ERR_INVALID_ARG, "shape index %d out of range", i);
+}
+
+void brev_reset_tuning(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  memset(g_tuned, 0, sizeof(g_tuned));
+  memset(g_tuned_gbs, 0, sizeof(g_tuned_gbs));
+}
+
+static bool device_identity(std::string* name, int* sms) {
+  int dev = 0;
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  *name = prop.name;
+  *sms = prop.multiProcessorCount;
+  return true;
+}
+
+static brev_status write_cache(const char* path) {
+  std::string name;
+  int sms = 0;
+  if (!device_identity(&name, &sms)) return set_error(BREV_ERR_CUDA, "no device to tag the cache");
+  FILE* f = fopen(path, "w");
+  if (!f) return set_error(BREV_ERR_INVALID_ARG, "cannot write %s: %s", path, strerror(errno));
+  fprintf(f, "{\"format\": \"brev-tune-1\", \"device\": \"%s\", \"sm_count\": %d, \"entries\": [",
+          name.c_str(), sms);
+  const int Es[5] = {16, 8, 4, 2, 1};
+  bool first = true;
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (int ei = 0; ei < 5; ++ei)
+    for (int ip = 0; ip < 2; ++ip)
+      for (int k = 0; k <= BREV_MAX_LOG2N; ++k) {
+        const int8_t* t = g_tuned[ei][ip][k];
+        if (t[0] <= 0) continue;
+        fprintf(f, "%s\n  {\"elem_bytes\": %d, \"log2n\": %d, \"in_place\": %d, \"bx\": %d, "
+                   "\"bz\": %d, \"gbs\": %.1f}",
+                first ? "" : ",", Es[ei], k, ip, t[0], t[1], g_tuned_gbs[ei][ip][k]);
+        first = false;
+      }
+  fprintf(f, "\n]}\n");
+  fclose(f);
+  return BREV_OK;
+}
+
+// Integer value of "key": in [b, e); returns false if absent.
+static bool json_int(const char* b, const char* e, const char* key, long* out) {
+  std::string pat = std::string("\"") + key + "\"";
+  const char* p = std::search(b, e, pat.begin(), pat.end());
+  if (p == e) return false;
+  p += pat.size();
+  while (p < e && (*p == ' ' || *p == ':' || *p == '\t' || *p == '\n')) ++p;
+  char* endp = nullptr;
+  long v = strtol(p, &endp, 10);
+  if (endp == p) return false;
+  *out = v;
+  return true;
+}
+
+static bool json_str(const char* b, const char* e, const char* key, std::string* out) {
+  std::string pat = std::string("\"") + key + "\"";
+  const char* p = std::search(b, e, pat.begin(), pat.end());
+  if (p == e) return false;
+  p += pat.size();
+  while (p < e && *p != '"') ++p;
+  if (p == e) return false;
+  const char* q = ++p;
+  while (q < e && *q != '"') ++q;
+  *out = std::string(p, q);
+  return true;
+}
+
+brev_status brev_load_tune_cache(const char* path) {
+  if (!path) return set_error(BREV_ERR_INVALID_ARG, "NULL path");
+  FILE* f = fopen(path, "rb");
+  if (!f) return set_error(BREV_ERR_INVALID_ARG, "cannot read %s: %s", path, strerror(errno));
+  std::string text;
+  char buf[4096];
+  size_t r;
+  while ((r = fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, r);
+  fclose(f);
+  const char* b = text.data();
+  const char* e = b + text.size();
+  const char* ent = strstr(b, "\"entries\"");
+  if (!ent) return set_error(BREV_ERR_INVALID_ARG, "%s: no \"entries\"", path);
+  std::string fname, dname;
+  long fsms = 0;
+  int dsms = 0;
+  json_str(b, ent, "device", &fname);
+  json_int(b, ent, "sm_count", &fsms);
+  // without a device the entries are taken as they are (host-only use)
+  if (device_identity(&dname, &dsms) && (fname != dname || fsms != dsms)) return BREV_OK;
+  int loaded = 0;
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (const char* p = strchr(ent, '{'); p; p = strchr(p, '{')) {
+    const char* q = strchr(p, '}');
+    if (!q) break;
+    long E = 0, k = -1, ip = -1, bx = 0, bz = 0;
+    if (json_int(p, q, "elem_bytes", &E) && json_int(p, q, "log2n", &k) &&
+        json_int(p, q, "in_place", &ip) && json_int(p, q, "bx", &bx) &&
+        json_int(p, q, "bz", &bz) && valid_E((int)E) && k >= 0 && k <= BREV_MAX_LOG2N &&
+        (ip == 0 || ip == 1) && bx > 0 && bz > 0 && bx + bz <= k && (ip == 0 || bx == bz) &&
+        find_shape((int)E, 16, (int)bx, (int)bz, (int)ip)) {
+      int8_t* t = g_tuned[e_index((int)E)][ip][k];
+      t[0] = (int8_t)bx;
+      t[1] = (int8_t)bz;
+      ++loaded;
+    }
+    p = q + 1;
+  }
+  return BREV_OK;
+}
+
+brev_status brev_autotune(int k_min, int k_max, int elem_bytes, const char* cache_path) {
+  if (!valid_E(elem_bytes)) return set_error(BREV_ERR_INVALID_ARG, "elem_bytes=%d", elem_bytes);
+  if (k_min < 0 || k_max > BREV_MAX_LOG2N || k_min > k_max)
+    return set_error(BREV_ERR_INVALID_ARG, "k range [%d, %d]", k_min, k_max);
+  const int E = elem_bytes;
+  const uint64_t max_bytes = (uint64_t)E << k_max;
+  cudaStream_t st = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_error(e, "autotune stream");
+  int dev = 0, l2 = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+  const size_t flush_bytes = std::max<size_t>(2ull * (size_t)l2, 64ull << 20);
+  void *a = nullptr, *b = nullptr, *fl = nullptr;
+  e = cudaMalloc(&a, max_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&b, max_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&fl, flush_bytes);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  brev_status result = BREV_OK;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    result = set_error(BREV_ERR_OOM, "autotune buffers: %s", cudaGetErrorString(e));
+  }
+  if (result == BREV_OK) {
+    cudaMemsetAsync(a, 0x5A, max_bytes, st);
+    for (int k = k_min; k <= k_max && result == BREV_OK; ++k) {
+      if (k < 2 * b_min_for(E)) continue;
+      const uint64_t bytes = (uint64_t)E << k;
+      const int reps = bytes >= (64ull << 20) ? 5 : 11;
+      for (int ip = 0; ip < 2 && result == BREV_OK; ++ip) {
+        int n = 0;
+        const ShapeEntry* t = table_for(E, &n);
+        double best = 1e30;
+        int bbx = 0, bbz = 0;
+        for (int i = 0; i < n; ++i) {
+          if (t[i].E != E || t[i].W != 16 || t[i].kind != ip || t[i].bx + t[i].bz > k) continue;
+          Choice c{false, &t[i]};
+          void* dst = ip ? a : b;
+          std::vector<float> ms;
+          for (int r = 0; r < reps + 2 && result == BREV_OK; ++r) {
+            cudaMemsetAsync(fl, r & 0xFF, flush_bytes, st);  // evict the array from L2
+            cudaEventRecord(e0, st);
+            result = launch_choice(c, dst, a, k, E, st);
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+              result = cuda_error(cudaGetLastError(), "autotune timing");
+              break;
+            }
+            float m = 0;
+            cudaEventElapsedTime(&m, e0, e1);
+            if (r >= 2) ms.push_back(m);  // two warm-up runs
+          }
+          if (result != BREV_OK) break;
+          std::sort(ms.begin(), ms.end());
+          const double med = ms[ms.size() / 2];
+          if (med < best) {
+            best = med;
+            bbx = t[i].bx;
+            bbz = t[i].bz;
+          }
+        }
+        if (bbx > 0) {
+          std::lock_guard<std::mutex> lk(g_mu);
+          g_tuned[e_index(E)][ip][k][0] = (int8_t)bbx;
+          g_tuned[e_index(E)][ip][k][1] = (int8_t)bbz;
+          g_tuned_gbs[e_index(E)][ip][k] = 2.0 * (double)bytes / (best * 1e-3) / 1e9;
+        }
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(st);
+  if (a) cudaFree(a);
+  if (b) cudaFree(b);
+  if (fl) cudaFree(fl);
+  cudaStreamDestroy(st);
+  if (result == BREV_OK && cache_path) result = write_cache(cache_path);
+  return result;
+}
+
+brev_status brev_get_device_info(brev_device_info* out) {
+  if (!out) return set_error(BREV_ERR_INVALID_ARG, "NULL output");
+  memset(out, 0, sizeof(*out));
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, dev);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetDeviceProperties");
+  snprintf(out->name, sizeof(out->name), "%s", prop.name);
+  cudaDeviceGetAttribute(&out->sm_count, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&out->l2_bytes, cudaDevAttrL2CacheSize, dev);
+  cudaDeviceGetAttribute(&out->mem_clock_khz, cudaDevAttrMemoryClockRate, dev);
+  cudaDeviceGetAttribute(&out->mem_bus_bits, cudaDevAttrGlobalMemoryBusWidth, dev);
+  cudaDeviceGetAttribute(&out->max_smem_per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  out->nominal_gbs = (double)out->mem_clock_khz * 1e3 * 2.0 * (out->mem_bus_bits / 8.0) / 1e9;
+  return BREV_OK;
+}
+
+uint64_t brev_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+const char* brev_status_string(brev_status s) {
+  switch (s) {
+    case BREV_OK: return "BREV_OK";
+    case BREV_ERR_INVALID_ARG: return "BREV_ERR_INVALID_ARG";
+    case BREV_ERR_ALIGNMENT: return "BREV_ERR_ALIGNMENT";
+    case BREV_ERR_OVERLAP: return "BREV_ERR_OVERLAP";
+    case BREV_ERR_OOM: return "BREV_ERR_OOM";
+    case BREV_ERR_CUDA: return "BREV_ERR_CUDA";
+    case BREV_ERR_UNSUPPORTED: return "BREV_ERR_UNSUPPORTED";
+  }
+  return "BREV_ERR_UNKNOWN";
+}
+
+const char* brev_last_error(void) { return t_last_error.c_str(); }
+
+int brev_version(void) { return BREV_VERSION; }
+
+}  // extern "C"

@@ -1,0 +1,366 @@
+// Batched in-place permutation of many independent arrays in one persistent
+// launch (no counterpart in the paper, whose methods take one array).
+//
+// Work decomposition: every array contributes units -- its tile pairs and
+// self-paired tiles (square tiles of exponent b), or one unit for a small
+// array staged whole -- and consecutive units of one array are grouped into
+// tickets of `grain` units.  Persistent CTAs (a full wave: SMs x resident
+// CTAs) take tickets from a global counter with atomicAdd, find the owning
+// array by a warp-parallel search over the descriptors' first-ticket
+// indices, and run the units with the same device bodies as the
+// single-array kernels.  The only cross-CTA interaction is the ticket
+// counter; there are no spin waits.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "brev_device.cuh"
+#include "brev_internal.h"
+
+namespace brev {
+
+struct BatchDesc {
+  char* ptr;
+  unsigned long long first_ticket;  // tickets [first_ticket, first_ticket + tickets)
+  unsigned units;                   // work units of this array
+  unsigned grain;                   // units per ticket
+  int k;
+  int E;
+  int b;                            // square tile exponent; 0 = whole array in one CTA
+  int pad_;
+};
+
+constexpr int BATCH_THREADS = 256;
+
+// Last descriptor whose first_ticket <= t (descriptors sorted by
+// first_ticket, strictly increasing, first one 0).  Run by one full warp:
+// each round the 32 lanes probe evenly spaced descriptors and the window
+// shrinks ~32x, so 4096 arrays need 3 rounds of one L2 load per lane.
+__device__ __forceinline__ int find_array(const BatchDesc* __restrict__ d, int count,
+                                          unsigned long long t) {
+  const int lane = threadIdx.x & 31;
+  int lo = 0, hi = count;
+  while (hi - lo > 1) {
+    const int span = hi - lo;
+    const int pos = lo + (int)(((long long)span * lane) >> 5);
+    const bool ok = d[pos].first_ticket <= t;
+    const unsigned m = __ballot_sync(0xffffffffu, ok);
+    const int last = 31 - __clz(m);
+    const int nlo = __shfl_sync(0xffffffffu, pos, last);
+    const int nhi = __shfl_sync(0xffffffffu, pos, last < 31 ? last + 1 : 31);
+    lo = nlo;
+    hi = last < 31 ? nhi : hi;
+  }
+  return lo;
+}
+
+template <int E, int B>
+__device__ __forceinline__ void run_tile_unit(const BatchDesc& d, unsigned u, uint4* sm) {
+  using G = Geom<E, 16, B, B>;
+  tile_inplace_body<G, BATCH_THREADS>(d.ptr, d.k, u, reinterpret_cast<uint4*>(sm));
+}
+
+__device__ __forceinline__ void run_unit(const BatchDesc& d, unsigned u, uint4* sm) {
+  switch (d.E) {
+    case 16:
+      switch (d.b) {
+        case 0: small_body<16>(d.ptr, d.ptr, d.k, BATCH_THREADS, sm); break;
+        case 3: run_tile_unit<16, 3>(d, u, sm); break;
+        case 4: run_tile_unit<16, 4>(d, u, sm); break;
+        case 5: run_tile_unit<16, 5>(d, u, sm); break;
+        case 6: run_tile_unit<16, 6>(d, u, sm); break;
+      }
+      break;
+    case 8:
+      switch (d.b) {
+        case 0: small_body<8>(d.ptr, d.ptr, d.k, BATCH_THREADS, reinterpret_cast<uint2*>(sm)); break;
+        case 4: run_tile_unit<8, 4>(d, u, sm); break;
+        case 5: run_tile_unit<8, 5>(d, u, sm); break;
+        case 6: run_tile_unit<8, 6>(d, u, sm); break;
+      }
+      break;
+    case 4:
+      switch (d.b) {
+        case 0: small_body<4>(d.ptr, d.ptr, d.k, BATCH_THREADS, reinterpret_cast<uint32_t*>(sm)); break;
+        case 5: run_tile_unit<4, 5>(d, u, sm); break;
+        case 6: run_tile_unit<4, 6>(d, u, sm); break;
+        case 7: run_tile_unit<4, 7>(d, u, sm); break;
+      }
+      break;
+  }
+}
+
+__global__ void __launch_bounds__(BATCH_THREADS)
+    k_batched(const BatchDesc* __restrict__ desc, int count, unsigned long long tickets,
+              unsigned long long* ticket_ctr) {
+  extern __shared__ uint4 smem_u4[];
+  __shared__ unsigned long long s_ticket;
+  __shared__ int s_array;
+  for (;;) {
+    if (threadIdx.x == 0) s_ticket = atomicAdd(ticket_ctr, 1ull);
+    __syncthreads();
+    const unsigned long long t = s_ticket;
+    if (t >= tickets) return;
+    if (threadIdx.x < 32) {
+      const int a = find_array(desc, count, t);
+      if (threadIdx.x == 0) s_array = a;
+    }
+    __syncthreads();
+    const BatchDesc d = desc[s_array];
+    const unsigned first = (unsigned)(t - d.first_ticket) * d.grain;
+    const unsigned last = min(first + d.grain, d.units);
+    for (unsigned u = first; u < last; ++u) {
+      run_unit(d, u, smem_u4);
+      __syncthreads();  // the next unit reuses the shared-memory tiles
+    }
+  }
+}
+
+// ------------------------------------------------------------------ host --
+
+static bool batched_shape_ok(int E, int b) {
+  switch (E) {
+    case 16: return b == 0 || (b >= 3 && b <= 6);
+    case 8: return b == 0 || (b >= 4 && b <= 6);
+    case 4: return b == 0 || (b >= 5 && b <= 7);
+  }
+  return false;
+}
+
+// Tile exponent for an in-place array in the batched kernel: the tuned or
+// default in-place shape of the single-array path, clamped to the bodies
+// compiled in above; 0 for arrays staged whole.
+static int batched_b(int k, int E) {
+  int bx = 0, bz = 0;
+  if (brev_tile_shape(k, E, 1, &bx, &bz) != BREV_OK) return -1;
+  if (bx == 0) return 0;
+  if (!batched_shape_ok(E, bx)) return -1;
+  return bx;
+}
+
+struct BatchPlanData {
+  std::vector<BatchDesc> desc;
+  unsigned long long tickets = 0;
+  unsigned smem = 0;
+  std::vector<BatchItem> fallback;  // arrays run with single-array launches
+};
+
+static brev_status build_batch(const BatchItem* items, int count, BatchPlanData* out) {
+  struct Tmp {
+    BatchDesc d;
+    unsigned long long bytes;
+  };
+  std::vector<Tmp> tmp;
+  tmp.reserve(count);
+  for (int i = 0; i < count; ++i) {
+    const BatchItem& it = items[i];
+    if (it.k <= 1) continue;  // identity
+    const bool vec = ((uintptr_t)it.ptr % 16) == 0;
+    const int b = (it.E == 4 || it.E == 8 || it.E == 16) && vec ? batched_b(it.k, it.E) : -1;
+    if (b < 0) {
+      out->fallback.push_back(it);
+      continue;
+    }
+    BatchDesc d{};
+    d.ptr = (char*)it.ptr;
+    d.k = it.k;
+    d.E = it.E;
+    d.b = b;
+    unsigned long long unit_bytes;
+    if (b == 0) {
+      d.units = 1;
+      unit_bytes = (unsigned long long)it.E << it.k;
+      out->smem = std::max<unsigned>(out->smem, (unsigned)unit_bytes);
+    } else {
+      const int w = it.k - 2 * b;
+      d.units = count_lt(w) + count_self(w);
+      unit_bytes = 2ull * ((unsigned long long)it.E << (2 * b));
+      out->smem = std::max<unsigned>(out->smem, (unsigned)unit_bytes);
+    }
+    // about 64 KiB of tile data per ticket
+    const unsigned long long g = std::max<unsigned long long>(1, 65536ull / unit_bytes);
+    d.grain = (unsigned)std::min<unsigned long long>(g, d.units);
+    tmp.push_back({d, (unsigned long long)it.E << it.k});
+  }
+  // largest arrays first: the long-running tickets start early and the
+  // small ones fill the tail
+  std::stable_sort(tmp.begin(), tmp.end(),
+                   [](const Tmp& a, const Tmp& b) { return a.bytes > b.bytes; });
+  unsigned long long t = 0;
+  out->desc.reserve(tmp.size());
+  for (auto& x : tmp) {
+    x.d.first_ticket = t;
+    t += (x.d.units + x.d.grain - 1) / x.d.grain;
+    out->desc.push_back(x.d);
+  }
+  out->tickets = t;
+  return BREV_OK;
+}
+
+static int batched_grid(unsigned smem) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched, BATCH_THREADS, smem) !=
+          cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  return per_sm * current_device_sm_count();
+}
+
+// Enqueue the ticket reset, the persistent kernel and the per-array
+// fallbacks on `stream` (which may be capturing).
+static brev_status enqueue_batch(const BatchPlanData& p, const BatchDesc* d_desc,
+                                 unsigned long long* d_ticket, cudaStream_t stream) {
+  if (!p.desc.empty()) {
+    cudaError_t e = cudaMemsetAsync(d_ticket, 0, sizeof(unsigned long long), stream);
+    if (e != cudaSuccess) return cuda_error(e, "ticket reset");
+    e = ensure_smem((const void*)k_batched, p.smem);
+    if (e != cudaSuccess) return cuda_error(e, "shared-memory limit of the batched kernel");
+    const int grid = (int)std::min<unsigned long long>(
+        (unsigned long long)batched_grid(p.smem), p.tickets);
+    int count = (int)p.desc.size();
+    unsigned long long tickets = p.tickets;
+    void* args[] = {(void*)&d_desc, (void*)&count, (void*)&tickets, (void*)&d_ticket};
+    e = cudaLaunchKernel((const void*)k_batched, dim3(grid), dim3(BATCH_THREADS), args, p.smem,
+                         stream);
+    if (e != cudaSuccess) return cuda_error(e, "batched kernel launch");
+    note_launch();
+  }
+  for (const BatchItem& it : p.fallback) {
+    brev_status s = launch_single(it.ptr, it.ptr, it.k, it.E, stream);
+    if (s != BREV_OK) return s;
+  }
+  return BREV_OK;
+}
+
+brev_status batched_launch(const BatchItem* items, int count, cudaStream_t stream) {
+  BatchPlanData p;
+  brev_status s = build_batch(items, count, &p);
+  if (s != BREV_OK) return s;
+  if (p.desc.empty()) return enqueue_batch(p, nullptr, nullptr, stream);
+  // stream-ordered workspace: descriptors + ticket counter
+  const size_t desc_bytes = p.desc.size() * sizeof(BatchDesc);
+  void* ws = nullptr;
+  cudaError_t e = cudaMallocAsync(&ws, desc_bytes + 64, stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(BREV_ERR_OOM, "batched workspace of %zu bytes: %s", desc_bytes + 64,
+                     cudaGetErrorString(e));
+  }
+  // pageable source: staged before the call returns
+  e = cudaMemcpyAsync(ws, p.desc.data(), desc_bytes, cudaMemcpyHostToDevice, stream);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(ws, stream);
+    return cuda_error(e, "descriptor upload");
+  }
+  auto* d_ticket = reinterpret_cast<unsigned long long*>((char*)ws + ((desc_bytes + 15) / 16) * 16);
+  s = enqueue_batch(p, (const BatchDesc*)ws, d_ticket, stream);
+  cudaFreeAsync(ws, stream);
+  return s;
+}
+
+}  // namespace brev
+
+// ------------------------------------------------------------------ plans --
+struct brev_plan {
+  brev::BatchPlanData data;
+  void* d_ws = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  uint64_t launches_per_replay = 0;
+  int device = -1;
+};
+
+using namespace brev;
+
+extern "C" brev_status brev_plan_create(void* const* ptr_array, const int* log2n_array,
+                                        const int* elem_bytes_array, int elem_bytes, int count,
+                                        brev_plan** out_plan) {
+  if (!out_plan) return set_error(BREV_ERR_INVALID_ARG, "out_plan is NULL");
+  *out_plan = nullptr;
+  if (count < 0 || (count > 0 && (!ptr_array || !log2n_array)))
+    return set_error(BREV_ERR_INVALID_ARG, "bad count or NULL arrays");
+  std::vector<BatchItem> items(count);
+  for (int i = 0; i < count; ++i) {
+    const int E = elem_bytes_array ? elem_bytes_array[i] : elem_bytes;
+    items[i] = BatchItem{ptr_array[i], log2n_array[i], E};
+  }
+  brev_status s = validate_batch_items(items.data(), count);
+  if (s != BREV_OK) return s;
+  brev_plan* p = new (std::nothrow) brev_plan();
+  if (!p) return set_error(BREV_ERR_OOM, "plan allocation");
+  cudaGetDevice(&p->device);
+  s = build_batch(items.data(), count, &p->data);
+  if (s != BREV_OK) {
+    delete p;
+    return s;
+  }
+  const size_t desc_bytes = p->data.desc.size() * sizeof(BatchDesc);
+  const size_t ticket_off = ((desc_bytes + 15) / 16) * 16;
+  cudaError_t e = cudaMalloc(&p->d_ws, ticket_off + 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete p;
+    return set_error(BREV_ERR_OOM, "plan workspace: %s", cudaGetErrorString(e));
+  }
+  if (desc_bytes) {
+    e = cudaMemcpy(p->d_ws, p->data.desc.data(), desc_bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      brev_plan_destroy(p);
+      return cuda_error(e, "plan descriptor upload");
+    }
+  }
+  cudaStream_t cs = nullptr;
+  e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    brev_plan_destroy(p);
+    return cuda_error(e, "capture stream");
+  }
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(cs);
+    brev_plan_destroy(p);
+    return cuda_error(e, "begin capture");
+  }
+  const uint64_t before = brev_launch_count();
+  s = enqueue_batch(p->data, (const BatchDesc*)p->d_ws,
+                    (unsigned long long*)((char*)p->d_ws + ticket_off), cs);
+  // captured launches run at each replay, not now
+  p->launches_per_replay = brev_launch_count() - before;
+  note_launch_adjust(-(int64_t)p->launches_per_replay);
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+  cudaStreamDestroy(cs);
+  if (s != BREV_OK || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    brev_plan_destroy(p);
+    return s != BREV_OK ? s : cuda_error(e2, "end capture");
+  }
+  p->graph = g;
+  e = cudaGraphInstantiate(&p->exec, g, 0);
+  if (e != cudaSuccess) {
+    brev_plan_destroy(p);
+    return cuda_error(e, "graph instantiate");
+  }
+  *out_plan = p;
+  return BREV_OK;
+}
+
+extern "C" brev_status brev_plan_launch(brev_plan* plan, void* stream) {
+  if (!plan || !plan->exec) return set_error(BREV_ERR_INVALID_ARG, "invalid plan");
+  cudaError_t e = cudaGraphLaunch(plan->exec, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_error(e, "graph launch");
+  note_launch(plan->launches_per_replay);
+  return BREV_OK;
+}
+
+extern "C" void brev_plan_destroy(brev_plan* plan) {
+  if (!plan) return;
+  if (plan->exec) cudaGraphExecDestroy(plan->exec);
+  if (plan->graph) cudaGraphDestroy(plan->graph);
+  if (plan->d_ws) cudaFree(plan->d_ws);
+  delete plan;
+}

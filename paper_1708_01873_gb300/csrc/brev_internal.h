@@ -1,0 +1,67 @@
+// Host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/brev.h"
+
+namespace brev {
+
+// One compiled tile kernel.  kind: 0 = out-of-place tile (grid = 2^(k-bx-bz)),
+// 1 = in-place pair/self units (grid = count_lt(w) + count_self(w)).
+struct ShapeEntry {
+  int E;        // element bytes
+  int W;        // access width: 16 (vector path) or E (element-wide path)
+  int bx, bz;   // tile = 2^bx source rows x 2^bz elements
+  int kind;
+  const void* kernel;
+  unsigned smem;   // dynamic shared memory per CTA
+  int threads;     // CTA size
+};
+
+// Tables defined in brev_shapes_*.cu.
+extern const ShapeEntry g_shapes_e16[];
+extern const int g_shapes_e16_n;
+extern const ShapeEntry g_shapes_e8[];
+extern const int g_shapes_e8_n;
+extern const ShapeEntry g_shapes_e4[];
+extern const int g_shapes_e4_n;
+extern const ShapeEntry g_shapes_e21[];
+extern const int g_shapes_e21_n;
+
+// Small-array kernel for element size E (brev_shapes_e21.cu).
+const void* small_kernel(int E);
+
+// Smallest square tile exponent whose rows are >= 128 bytes.
+inline int b_min_for(int E) {
+  int b = 0;
+  while ((E << b) < 128) ++b;
+  return b;
+}
+
+// Launch bookkeeping (brev_api.cu).
+void note_launch(uint64_t n = 1);
+void note_launch_adjust(int64_t delta);
+brev_status set_error(brev_status s, const char* fmt, ...);
+brev_status cuda_error(cudaError_t e, const char* what);
+// Raise the dynamic shared-memory limit of `kernel` to `smem` on the
+// current device (once per kernel and device).
+cudaError_t ensure_smem(const void* kernel, unsigned smem);
+int current_device_sm_count();
+// Validate a device range (device or managed memory, inside one allocation).
+brev_status check_device_range(const void* p, uint64_t bytes, const char* what);
+
+// Batched work (brev_batched.cu).
+struct BatchItem {
+  void* ptr;
+  int k;
+  int E;
+};
+brev_status batched_launch(const BatchItem* items, int count, cudaStream_t stream);
+// Argument checks of a batch (sizes, alignment, device ranges, no overlap).
+brev_status validate_batch_items(const BatchItem* items, int count);
+// Launch one permutation without argument checks (src == dst: in-place).
+brev_status launch_single(void* dst, const void* src, int k, int E, cudaStream_t stream);
+
+}  // namespace brev

@@ -1,0 +1,288 @@
+"""CPU emulation of the tile kernels' index arithmetic (no GPU).
+
+Replays, for every thread of every CTA, the global and shared-memory
+addresses that the tile kernels compute (same formulas, written again in
+Python from the kernel design: x y z split, rows at rev(x) in shared memory,
+XOR swizzle, V x V register transpose, pair/self unit enumeration) and
+checks that
+
+  * every global access stays inside the 2^k-element buffer and every
+    shared-memory access inside the CTA's allocation,
+  * each source element is loaded exactly once and each destination
+    element written exactly once,
+  * shared-memory rows are written without bank conflicts and read without
+    bank conflicts (per 128-byte wavefront),
+  * the resulting permutation equals the CPU oracle.
+
+This is the check run before any kernel goes to a GPU.
+"""
+import numpy as np
+import pytest
+
+import pins
+
+
+def brev(v, w):
+    return pins.brute_rev(v, w) if w else 0
+
+
+def count_lt(w):
+    return (1 << (w - 1)) - (1 << ((w + 1) // 2 - 1)) if w >= 1 else 0
+
+
+def count_self(w):
+    return 1 << ((w + 1) // 2)
+
+
+def unrank_lt(q, w):
+    outer = 0
+    d = 0
+    while 2 * d + 2 <= w:
+        rem = w - 2 * d
+        c01 = 1 << (rem - 2)
+        if q < c01:
+            return outer | (q << (d + 1)) | (1 << d)
+        q -= c01
+        r2 = count_lt(rem - 2)
+        if q >= r2:
+            q -= r2
+            outer |= (1 << (w - 1 - d)) | (1 << d)
+        d += 1
+    return outer
+
+
+def unrank_self(p, w):
+    a = (w + 1) // 2
+    lw = w - a
+    return (p << lw) | brev(p >> (a - lw), lw)
+
+
+class Geom:
+    def __init__(self, E, W, BX, BZ):
+        self.E, self.W, self.BX, self.BZ = E, W, BX, BZ
+        self.V = W // E
+        self.CIN = (1 << BZ) // self.V
+        self.COUT = (1 << BX) // self.V
+        assert self.CIN * W >= 128 and self.COUT * W >= 128
+        self.CHUNKS = (1 << BX) * self.CIN
+        self.UNITS = self.CIN * self.COUT
+        self.THREADS = min(self.UNITS, 256)
+        self.PHASE = 128 // W
+        self.SWZ = self.PHASE - 1
+
+
+def emulate_tile(G, k, nthr, src_tiles, dst_tiles, row_stride_in, row_stride_out,
+                 n_elems, loads, stores, conflicts):
+    """One CTA: load NT tiles (element offsets of their (x=0, z=0) corner),
+    then store tile t to dst_tiles[t].  Records element moves."""
+    smem = {}
+    per = (G.CHUNKS + nthr - 1) // nthr
+    for t, base in enumerate(src_tiles):
+        # load phase, per warp instruction: lanes of one i
+        for i in range(per):
+            slots = []
+            for tid in range(nthr):
+                q = tid + i * nthr
+                if q >= G.CHUNKS:
+                    continue
+                x, c = q // G.CIN, q % G.CIN
+                for e in range(G.V):
+                    g = base + x * row_stride_in + c * G.V + e
+                    assert 0 <= g < n_elems
+                    loads.append(g)
+                X = brev(x, G.BX)
+                pc = c ^ ((X // G.V) & G.SWZ)
+                assert 0 <= pc < G.CIN
+                s = t * G.CHUNKS + X * G.CIN + pc
+                assert 0 <= s < len(src_tiles) * G.CHUNKS
+                smem[s] = [(base + x * row_stride_in + c * G.V + e) for e in range(G.V)]
+                slots.append((tid, s))
+            conflicts.append(_wavefront_conflicts(slots, G.W))
+    for t, dbase in enumerate(dst_tiles):
+        per_u = (G.UNITS + nthr - 1) // nthr
+        for i in range(per_u):
+            for j in range(G.V):
+                slots = []
+                for tid in range(nthr):
+                    u = tid + i * nthr
+                    if u >= G.UNITS:
+                        continue
+                    c, d = u // G.COUT, u % G.COUT
+                    pc = c ^ (d & G.SWZ)
+                    s = t * G.CHUNKS + (d * G.V + j) * G.CIN + pc
+                    slots.append((tid, s))
+                conflicts.append(_wavefront_conflicts(slots, G.W))
+            for tid in range(nthr):
+                u = tid + i * nthr
+                if u >= G.UNITS:
+                    continue
+                c, d = u // G.COUT, u % G.COUT
+                pc = c ^ (d & G.SWZ)
+                blk = [smem[t * G.CHUNKS + (d * G.V + j) * G.CIN + pc] for j in range(G.V)]
+                for e in range(G.V):
+                    Z = brev(c * G.V + e, G.BZ)
+                    for j in range(G.V):
+                        g = dbase + Z * row_stride_out + d * G.V + j
+                        assert 0 <= g < n_elems
+                        stores.append((g, blk[j][e]))
+
+
+def _wavefront_conflicts(slots, W):
+    """Extra wavefronts beyond the minimum for one warp-wide shared access of
+    W bytes per lane (slots: (lane, chunk index)), per warp."""
+    extra = 0
+    by_warp = {}
+    for tid, s in slots:
+        by_warp.setdefault(tid // 32, []).append(s)
+    for chunks in by_warp.values():
+        # bank of each 4-byte word touched
+        words = {}
+        for s in chunks:
+            b0 = s * W
+            for w in range(max(1, W // 4)):
+                addr = b0 + 4 * w
+                words.setdefault((addr // 4) % 32, set()).add(addr // 4)
+        need = max(len(v) for v in words.values())
+        minimum = max(1, (len(chunks) * W + 127) // 128)
+        extra += max(0, need - minimum)
+    return extra
+
+
+SHAPES = {
+    16: [(3, 3), (4, 4), (5, 5), (6, 6), (4, 5), (5, 4), (5, 6), (6, 5)],
+    8: [(4, 4), (5, 5), (6, 6), (4, 5), (5, 4), (5, 6), (6, 5)],
+    4: [(5, 5), (6, 6), (7, 7), (5, 6), (6, 5), (6, 7), (7, 6)],
+    2: [(6, 6), (7, 7)],
+    1: [(7, 7), (8, 8)],
+}
+WIDE = {8: [(4, 4), (5, 5)], 4: [(5, 5), (6, 6)], 2: [(6, 6)], 1: [(7, 7)]}
+
+
+def run_oop(E, W, bx, bz, k, nthr=None):
+    G = Geom(E, W, bx, bz)
+    nthr = nthr or G.THREADS
+    n = 1 << k
+    wy = k - bx - bz
+    loads, stores, conflicts = [], [], []
+    for y in range(1 << wy):
+        ry = brev(y, wy)
+        emulate_tile(G, k, nthr, [y << bz], [ry << bx], 1 << (k - bx), 1 << (k - bz), n,
+                     loads, stores, conflicts)
+    return G, loads, stores, conflicts
+
+
+def run_inplace(E, W, b, k, nthr=None):
+    G = Geom(E, W, b, b)
+    nthr = nthr or G.THREADS
+    n = 1 << k
+    w = k - 2 * b
+    loads, stores, conflicts = [], [], []
+    units = count_lt(w) + count_self(w)
+    seen = set()
+    for q in range(units):
+        if q < count_lt(w):
+            y = unrank_lt(q, w)
+            ry = brev(y, w)
+            assert y < ry
+            src, dst = [y << b, ry << b], [ry << b, y << b]
+        else:
+            y = unrank_self(q - count_lt(w), w)
+            assert y == brev(y, w)
+            src, dst = [y << b], [y << b]
+        assert y not in seen
+        seen.add(y)
+        seen.add(brev(y, w))
+        emulate_tile(G, k, nthr, src, dst, 1 << (k - b), 1 << (k - b), n, loads, stores,
+                     conflicts)
+    assert len(seen) == 1 << w  # every tile covered exactly once
+    return G, loads, stores, conflicts
+
+
+def check_result(k, loads, stores):
+    n = 1 << k
+    assert sorted(loads) == list(range(n)), "each source element loaded once"
+    dsts = sorted(g for g, _ in stores)
+    assert dsts == list(range(n)), "each destination element written once"
+    perm = np.empty(n, dtype=np.int64)
+    for g, s in stores:
+        perm[g] = s
+    exp = np.array([brev(j, k) for j in range(n)])
+    assert np.array_equal(perm, exp)
+
+
+@pytest.mark.parametrize("E", sorted(SHAPES))
+def test_oop_index_math(E):
+    for bx, bz in SHAPES[E]:
+        for k in sorted({bx + bz, bx + bz + 1, bx + bz + 2}):
+            if (1 << k) > (1 << 17):
+                continue
+            G, loads, stores, conf = run_oop(E, 16, bx, bz, k)
+            check_result(k, loads, stores)
+            assert sum(conf) == 0, (E, bx, bz, k)
+
+
+@pytest.mark.parametrize("E", sorted(SHAPES))
+def test_inplace_index_math(E):
+    for b in sorted({bx for bx, bz in SHAPES[E] if bx == bz}):
+        for k in sorted({2 * b, 2 * b + 1, 2 * b + 2, 2 * b + 3}):
+            if (1 << k) > (1 << 17):
+                continue
+            G, loads, stores, conf = run_inplace(E, 16, b, k)
+            check_result(k, loads, stores)
+            assert sum(conf) == 0, (E, b, k)
+
+
+@pytest.mark.parametrize("E", sorted(WIDE))
+def test_element_wide_index_math(E):
+    for b, _ in WIDE[E]:
+        k = 2 * b + 1
+        G, loads, stores, conf = run_oop(E, E, b, b, k)
+        check_result(k, loads, stores)
+        G, loads, stores, conf = run_inplace(E, E, b, k)
+        check_result(k, loads, stores)
+
+
+def test_batched_thread_count_index_math():
+    """The batched kernel runs the in-place bodies with 256 threads even when
+    the tile has fewer units (guards on q and u)."""
+    for E, b in ((16, 3), (16, 5), (8, 4), (4, 5), (4, 7)):
+        k = 2 * b + 2
+        G, loads, stores, _ = run_inplace(E, 16, b, k, nthr=256)
+        check_result(k, loads, stores)
+
+
+def test_unranking_enumerates_pairs_and_palindromes():
+    for w in range(0, 15):
+        lt = [unrank_lt(q, w) for q in range(count_lt(w))]
+        assert sorted(lt) == [y for y in range(1 << w) if y < brev(y, w)]
+        pal = [unrank_self(p, w) for p in range(count_self(w))]
+        assert sorted(pal) == [y for y in range(1 << w) if y == brev(y, w)]
+
+
+def find_array(first_ticket, t):
+    """Warp-parallel search of the batched kernel, lane by lane."""
+    lo, hi = 0, len(first_ticket)
+    rounds = 0
+    while hi - lo > 1:
+        span = hi - lo
+        pos = [lo + ((span * lane) >> 5) for lane in range(32)]
+        ok = [first_ticket[p] <= t for p in pos]
+        assert all(0 <= p < len(first_ticket) for p in pos)
+        last = max(l for l in range(32) if ok[l])
+        nlo = pos[last]
+        nhi = pos[last + 1] if last < 31 else hi
+        lo, hi = nlo, nhi
+        rounds += 1
+        assert rounds < 10
+    return lo
+
+
+def test_batched_array_search():
+    rng = np.random.default_rng(3)
+    for count in (1, 2, 3, 31, 32, 33, 100, 4096):
+        sizes = rng.integers(1, 50, size=count)
+        first = np.concatenate([[0], np.cumsum(sizes)[:-1]]).tolist()
+        total = int(sizes.sum())
+        for t in list(range(0, min(total, 300))) + rng.integers(0, total, 300).tolist():
+            a = find_array(first, int(t))
+            assert first[a] <= t < (first[a + 1] if a + 1 < count else total)
