@@ -182,7 +182,9 @@ def run_brev(args):
     build()
     info = brev.brev_get_device_info()
     peak, peak_src = measured_peak()
-    stream = torch.cuda.current_stream(device)
+    # all work on one non-default stream (graph capture needs one)
+    stream = torch.cuda.Stream(device)
+    torch.cuda.set_stream(stream)
     sh = stream.cuda_stream
 
     def barrier():
@@ -207,7 +209,11 @@ def run_brev(args):
             launch_point(brev, p, ip, sh)
     torch.cuda.synchronize(device)
 
-    sampler = ClockSampler(local)
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(device).uuid)
+    except Exception:
+        gpu_id = str(local)
+    sampler = ClockSampler(gpu_id)
     sampler.start()
     time.sleep(0.3)
 
@@ -378,9 +384,13 @@ def bench_batched(torch, brev, inputs, device, stream, sampler, max_over_ranks, 
 
     # the loop of single launches captured into a CUDA graph too
     g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g, stream=stream):
+    cap = torch.cuda.Stream(device)
+    torch.cuda.synchronize(device)
+    c0 = L.brev_launch_count()
+    with torch.cuda.graph(g, stream=cap, capture_error_mode="thread_local"):
         for p, k, E in zip(ptrs, kk, ee):
-            L.brev_permute_to(p, p, k, E, torch.cuda.current_stream().cuda_stream)
+            L.brev_permute_to(p, p, k, E, cap.cuda_stream)
+    loop_launches = L.brev_launch_count() - c0
 
     def loop_graph():
         g.replay()
@@ -405,7 +415,7 @@ def bench_batched(torch, brev, inputs, device, stream, sampler, max_over_ranks, 
     plan.close()
     res = {"workload": "4096 arrays, k uniform in [8,20], E uniform in {8,16} (seed 4), "
                        "in place; persistent = one launch per batch",
-           "bytes_per_batch": total, **out,
+           "bytes_per_batch": total, "launches_in_loop": int(loop_launches), **out,
            "speedup_persistent_graph_vs_loop": round(out["loop"]["ms"] /
                                                      out["persistent_graph"]["ms"], 2),
            "speedup_persistent_graph_vs_loop_graph": round(out["loop_graph"]["ms"] /

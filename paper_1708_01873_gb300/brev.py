@@ -85,7 +85,20 @@ def lib() -> ctypes.CDLL:
                 f.restype = res
                 f.argtypes = args
             _lib = L
+            _load_default_tuning(L)
     return _lib
+
+
+DEFAULT_TUNE_CACHE = os.path.join(_HERE, "tune_gb300.json")
+
+
+def _load_default_tuning(L) -> None:
+    """Tuned tile shapes: $BREV_TUNE_CACHE if set, else the cache shipped
+    with the package (ignored by the library unless the device name and SM
+    count match the GPU it was tuned on)."""
+    path = os.environ.get("BREV_TUNE_CACHE", DEFAULT_TUNE_CACHE)
+    if path and os.path.exists(path):
+        L.brev_load_tune_cache(path.encode())
 
 
 def _check(status: int, func: str) -> None:
