@@ -113,6 +113,32 @@ BREV_API brev_status brev_plan_create(void *const *ptr_array, const int *log2n_a
 BREV_API brev_status brev_plan_launch(brev_plan *plan, void *stream);
 BREV_API void brev_plan_destroy(brev_plan *plan);
 
+/* No-allocation form of brev_permute_batched_mixed.  The paper has no
+ * counterpart: it exists for callers that cannot allocate device memory --
+ * code whose device memory is entirely handed to another allocator (a
+ * framework's caching pool, a fixed arena), or latency-critical loops in
+ * which a cudaMalloc, which can synchronise the device and can fail under
+ * fragmentation, is not acceptable.  Same arguments and result as
+ * brev_permute_batched_mixed, but the call allocates nothing: its scratch
+ * (ticket counter and per-array descriptors) is a fixed device array inside
+ * the library of 256 + BREV_NOALLOC_MAX_ARRAYS * 40 bytes (about 41 KiB),
+ * which every GPU that loads the library holds until the process exits.
+ *   - count > BREV_NOALLOC_MAX_ARRAYS returns BREV_ERR_INVALID_ARG.
+ *   - The first call on a device looks up the array's device address (once
+ *     per device, with that device current); make that first call before
+ *     any stream capture.
+ *   - Every call on a device shares that device's one array and overwrites
+ *     the previous call's contents (descriptors uploaded and counter zeroed
+ *     on `stream`), so calls ordered on one stream are safe, while calls
+ *     that overlap on the GPU (for example on two streams) race.
+ *   - Arrays of 1- or 2-byte elements, or not 16-byte aligned, are permuted
+ *     by single-array launches within the call (these allocate no device
+ *     memory either). */
+#define BREV_NOALLOC_MAX_ARRAYS 1024
+BREV_API brev_status brev_permute_batched_noalloc(void *const *ptr_array, const int *log2n_array,
+                                                  const int *elem_bytes_array, int count,
+                                                  void *stream);
+
 /* ---------------------------------------------------------------- host path */
 
 /* End-to-end form for host buffers: copies src_host (2^log2n elements) to

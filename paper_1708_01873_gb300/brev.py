@@ -41,6 +41,7 @@ SIGNATURES = {
     "brev_permute": (_i, [_vp, _i, _i, _i, _vp]),
     "brev_permute_batched": (_i, [_vpp, _ip, _i, _i, _vp]),
     "brev_permute_batched_mixed": (_i, [_vpp, _ip, _ip, _i, _vp]),
+    "brev_permute_batched_noalloc": (_i, [_vpp, _ip, _ip, _i, _vp]),
     "brev_plan_create": (_i, [_vpp, _ip, _ip, _i, _i, ctypes.POINTER(_vp)]),
     "brev_plan_launch": (_i, [_vp, _vp]),
     "brev_plan_destroy": (None, [_vp]),
@@ -187,6 +188,20 @@ def brev_permute_batched(tensors: Sequence, stream=None) -> None:
 
 
 brev_permute_batched_mixed = brev_permute_batched
+
+
+def brev_permute_batched_noalloc(tensors: Sequence, stream=None) -> None:
+    """The batched in-place permutation for callers that cannot allocate
+    device memory: its scratch is a fixed array inside the library (at most
+    BREV_NOALLOC_MAX_ARRAYS = 1024 arrays per call; calls that overlap on the
+    GPU race).  Make the first call on a device before any stream capture."""
+    tensors = list(tensors)
+    if not tensors:
+        return
+    ptrs, ks, es = _batch_arrays(tensors)
+    _check(lib().brev_permute_batched_noalloc(ptrs, ks, es, len(tensors),
+                                              _stream_handle(stream, tensors[0].device)),
+           "brev_permute_batched_noalloc")
 
 
 class BrevPlan:

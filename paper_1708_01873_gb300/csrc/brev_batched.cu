@@ -364,3 +364,177 @@ extern "C" void brev_plan_destroy(brev_plan* plan) {
   if (plan->d_ws) cudaFree(plan->d_ws);
   delete plan;
 }
+
+// ----------------------------------------------------- no-alloc variant --
+// brev_permute_batched_noalloc: the batched launch above for callers that
+// cannot allocate device memory.  Its scratch -- the ticket counter and the
+// descriptor table that every other batched call places in stream-ordered
+// workspace -- lives in the fixed device array below instead.  The array
+// is part of the library's module, so every GPU that loads the library
+// holds its NOALLOC_SCRATCH_BYTES until the process exits.
+namespace brev {
+
+constexpr int NOALLOC_MAX_ARRAYS = BREV_NOALLOC_MAX_ARRAYS;
+constexpr size_t NOALLOC_DESC_OFFSET = 256;  // ticket counter in the first 256 bytes
+constexpr size_t NOALLOC_SCRATCH_BYTES =
+    NOALLOC_DESC_OFFSET + (size_t)NOALLOC_MAX_ARRAYS * sizeof(BatchDesc);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+// Host code cannot use g_noalloc_scratch as a device address (its name in
+// host code is only a stand-in), so the address is looked up once per
+// device with that device current and cached here.
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[NOALLOC_MAX_DEVICES];
+
+static brev_status noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES)
+    return set_error(BREV_ERR_UNSUPPORTED, "device %d beyond the no-alloc table", dev);
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return cuda_error(e, "cudaGetSymbolAddress of the scratch array");
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return BREV_OK;
+}
+
+// Host-side staging in one fixed static block (guarded by g_noalloc_mu for
+// the whole call): nothing is allocated on the host either.
+struct NoallocHost {
+  BatchDesc desc[NOALLOC_MAX_ARRAYS];
+  BatchItem fallback[NOALLOC_MAX_ARRAYS];
+  unsigned long long bytes[NOALLOC_MAX_ARRAYS];
+  int order[NOALLOC_MAX_ARRAYS];
+  uint64_t lo[NOALLOC_MAX_ARRAYS], len[NOALLOC_MAX_ARRAYS];
+  int range_order[NOALLOC_MAX_ARRAYS];
+  BatchDesc sorted[NOALLOC_MAX_ARRAYS];
+};
+static NoallocHost g_noalloc_host;
+static std::mutex g_noalloc_call_mu;
+
+}  // namespace brev
+
+extern "C" brev_status brev_permute_batched_noalloc(void* const* ptr_array,
+                                                    const int* log2n_array,
+                                                    const int* elem_bytes_array, int count,
+                                                    void* stream) {
+  if (count < 0) return set_error(BREV_ERR_INVALID_ARG, "count=%d", count);
+  if (count > NOALLOC_MAX_ARRAYS)
+    return set_error(BREV_ERR_INVALID_ARG,
+                     "count=%d exceeds the %d arrays the fixed scratch of "
+                     "brev_permute_batched_noalloc holds",
+                     count, NOALLOC_MAX_ARRAYS);
+  if (count == 0) return BREV_OK;
+  if (!ptr_array || !log2n_array || !elem_bytes_array)
+    return set_error(BREV_ERR_INVALID_ARG, "NULL host array");
+  std::lock_guard<std::mutex> call_lock(g_noalloc_call_mu);
+  NoallocHost& h = g_noalloc_host;
+  cudaStream_t st = (cudaStream_t)stream;
+  // argument checks, array by array, then pairwise overlap on sorted ranges
+  for (int i = 0; i < count; ++i) {
+    const BatchItem it{ptr_array[i], log2n_array[i], elem_bytes_array[i]};
+    if (!(it.E == 1 || it.E == 2 || it.E == 4 || it.E == 8 || it.E == 16))
+      return set_error(BREV_ERR_INVALID_ARG, "array %d: elem_bytes=%d", i, it.E);
+    if (it.k < 0 || it.k > BREV_MAX_LOG2N)
+      return set_error(BREV_ERR_INVALID_ARG, "array %d: log2n=%d", i, it.k);
+    if (!it.ptr) return set_error(BREV_ERR_INVALID_ARG, "array %d: NULL pointer", i);
+    if ((uintptr_t)it.ptr % it.E)
+      return set_error(BREV_ERR_ALIGNMENT, "array %d: pointer not aligned to %d bytes", i, it.E);
+    brev_status s = check_device_range(it.ptr, (uint64_t)it.E << it.k, "array");
+    if (s != BREV_OK) return s;
+    h.lo[i] = (uint64_t)(uintptr_t)it.ptr;
+    h.len[i] = (uint64_t)it.E << it.k;
+    h.range_order[i] = i;
+  }
+  std::sort(h.range_order, h.range_order + count,
+            [&h](int a, int b) { return h.lo[a] < h.lo[b]; });
+  for (int i = 1; i < count; ++i) {
+    const int a = h.range_order[i - 1], b = h.range_order[i];
+    if (h.lo[a] + h.len[a] > h.lo[b])
+      return set_error(BREV_ERR_OVERLAP, "two arrays of the batch overlap");
+  }
+  // descriptors (the same decomposition as brev_permute_batched_mixed)
+  int nd = 0, nf = 0;
+  unsigned smem = 0;
+  for (int i = 0; i < count; ++i) {
+    const BatchItem it{ptr_array[i], log2n_array[i], elem_bytes_array[i]};
+    if (it.k <= 1) continue;
+    const bool vec = ((uintptr_t)it.ptr % 16) == 0;
+    const int b = (it.E == 4 || it.E == 8 || it.E == 16) && vec ? batched_b(it.k, it.E) : -1;
+    if (b < 0) {
+      h.fallback[nf++] = it;
+      continue;
+    }
+    BatchDesc d{};
+    d.ptr = (char*)it.ptr;
+    d.k = it.k;
+    d.E = it.E;
+    d.b = b;
+    unsigned long long unit_bytes;
+    if (b == 0) {
+      d.units = 1;
+      unit_bytes = (unsigned long long)it.E << it.k;
+    } else {
+      const int w = it.k - 2 * b;
+      d.units = count_lt(w) + count_self(w);
+      unit_bytes = 2ull * ((unsigned long long)it.E << (2 * b));
+    }
+    smem = std::max<unsigned>(smem, (unsigned)unit_bytes);
+    const unsigned long long g = std::max<unsigned long long>(1, 65536ull / unit_bytes);
+    d.grain = (unsigned)std::min<unsigned long long>(g, d.units);
+    h.desc[nd] = d;
+    h.bytes[nd] = (unsigned long long)it.E << it.k;
+    h.order[nd] = nd;
+    ++nd;
+  }
+  if (nd > 0) {
+    std::sort(h.order, h.order + nd, [&h](int a, int b) {
+      return h.bytes[a] != h.bytes[b] ? h.bytes[a] > h.bytes[b] : a < b;
+    });
+    unsigned long long tickets = 0;
+    for (int i = 0; i < nd; ++i) {
+      BatchDesc d = h.desc[h.order[i]];
+      d.first_ticket = tickets;
+      tickets += (d.units + d.grain - 1) / d.grain;
+      h.sorted[i] = d;
+    }
+    void* scratch = nullptr;
+    brev_status s = noalloc_scratch(&scratch);
+    if (s != BREV_OK) return s;
+    auto* d_ticket = reinterpret_cast<unsigned long long*>(scratch);
+    auto* d_desc = reinterpret_cast<const BatchDesc*>((char*)scratch + NOALLOC_DESC_OFFSET);
+    // the array keeps the previous call's contents: upload this call's
+    // descriptors and zero the ticket counter, in stream order
+    cudaError_t e = cudaMemcpyAsync((void*)d_desc, h.sorted, (size_t)nd * sizeof(BatchDesc),
+                                    cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_error(e, "descriptor upload (no-alloc)");
+    e = cudaMemsetAsync(d_ticket, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return cuda_error(e, "ticket reset (no-alloc)");
+    if (smem > 48 * 1024) {
+      e = cudaFuncSetAttribute((const void*)k_batched,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return cuda_error(e, "shared-memory limit (no-alloc)");
+    }
+    const int grid = (int)std::min<unsigned long long>((unsigned long long)batched_grid(smem),
+                                                       tickets);
+    int cnt = nd;
+    void* args[] = {(void*)&d_desc, (void*)&cnt, (void*)&tickets, (void*)&d_ticket};
+    e = cudaLaunchKernel((const void*)k_batched, dim3(grid), dim3(BATCH_THREADS), args, smem,
+                         st);
+    if (e != cudaSuccess) return cuda_error(e, "batched kernel launch (no-alloc)");
+    note_launch();
+  }
+  for (int i = 0; i < nf; ++i) {
+    brev_status s = launch_single(h.fallback[i].ptr, h.fallback[i].ptr, h.fallback[i].k,
+                                  h.fallback[i].E, st);
+    if (s != BREV_OK) return s;
+  }
+  return BREV_OK;
+}
