@@ -50,6 +50,10 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=90.0,
+                    help="total oracle time budget of --impl reference")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--no-serve", action="store_true")
     return ap.parse_args()
 
 
@@ -58,6 +62,23 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The slowest rank's time (the whole job ends when it does)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gbs(bytes_per_rank: float, world: int, seconds_max: float) -> float:
+    """Aggregate throughput: every rank's bytes over the slowest rank's time
+    (weak scaling: each rank runs the full per-GPU workload)."""
+    return world * bytes_per_rank / seconds_max / 1e9
 
 
 def measured_peak():
@@ -192,12 +213,8 @@ def run_brev(args):
             dist.barrier()
         torch.cuda.synchronize(device)
 
-    def max_over_ranks(x):
-        if ws == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def reduce_max(x):
+        return max_over_ranks(x, ws, device)
 
     pts = make_sweep(torch, inputs, args.kmax, device)
     seq = sweep_order(pts)
@@ -236,9 +253,9 @@ def run_brev(args):
     w1 = time.time()
     sampler.window(w0, w1)
     launches = L.brev_launch_count() - c0
-    ms_total = max_over_ranks(t_start.elapsed_time(t_end))
+    ms_total = reduce_max(t_start.elapsed_time(t_end))
     ms_per_step = ms_total / args.steps
-    value = ws * step_bytes * args.steps / (ms_total * 1e-3) / 1e9
+    value = whole_job_gbs(step_bytes * args.steps, ws, ms_total * 1e-3)
 
     # per-kernel aggregates from the per-launch events
     per_kernel = {}
@@ -277,14 +294,28 @@ def run_brev(args):
     # ---------------------------------------------------- batched (cfg 4)
     batched = None
     if not args.no_batched:
-        batched = bench_batched(torch, brev, inputs, device, stream, sampler, max_over_ranks,
+        batched = bench_batched(torch, brev, inputs, device, stream, sampler, reduce_max,
                                 barrier)
 
     # ------------------------------------------------------------ e2e
     e2e = None
     if not args.no_e2e:
         e2e = bench_e2e(torch, brev, inputs, pts, seq, args.e2e_steps, stream, sampler,
-                        max_over_ranks, barrier, ws)
+                        reduce_max, barrier, ws)
+    # ---------------------------------------------------- serving (cfg 5)
+    serving = None
+    if not args.no_serve:
+        from paper_1708_01873_gb300.serve import serve_poisson
+        for p in pts:  # release the sweep's buffers for the serving pool
+            p["src"] = p["dst"] = None
+        torch.cuda.empty_cache()
+        w0 = time.time()
+        serving = serve_poisson(seconds=args.serve_seconds, rate=20000.0, seed=5,
+                                pool_bytes=16 << 30, device=local)
+        sampler.window(w0, time.time())
+        serving["workload"] = ("Poisson arrivals, mean 50 us apart (20k req/s), k uniform in "
+                               "[10,24], E uniform in {4,8,16}, seed 5; pool 16 GiB, 256 slots, "
+                               "4 streams; latency = device completion - arrival")
     sampler.stop()
     clocks = sampler.summary()
 
@@ -316,6 +347,7 @@ def run_brev(args):
             "frac_of_nominal": round(value / ws / info["nominal_gbs"], 4),
             "large_arrays_gbs": large,
             "batched": batched,
+            "serving": serving,
             "e2e": e2e,
             "gpu_launches": int(launches),
             "clocks": clocks,
@@ -351,7 +383,7 @@ def load_traffic(kernel_name):
     return None
 
 
-def bench_batched(torch, brev, inputs, device, stream, sampler, max_over_ranks, barrier,
+def bench_batched(torch, brev, inputs, device, stream, sampler, reduce_max, barrier,
                   reps=10, warm=3):
     import numpy as np
     rng = np.random.default_rng(4)
@@ -410,7 +442,7 @@ def bench_batched(torch, brev, inputs, device, stream, sampler, max_over_ranks, 
         eb.record(stream)
         barrier()
         sampler.window(w0, time.time())
-        ms = max_over_ranks(ea.elapsed_time(eb)) / reps
+        ms = reduce_max(ea.elapsed_time(eb)) / reps
         out[name] = {"ms": round(ms, 3), "gbs": round(total / (ms * 1e-3) / 1e9, 1)}
     plan.close()
     res = {"workload": "4096 arrays, k uniform in [8,20], E uniform in {8,16} (seed 4), "
@@ -424,7 +456,7 @@ def bench_batched(torch, brev, inputs, device, stream, sampler, max_over_ranks, 
     return res
 
 
-def bench_e2e(torch, brev, inputs, pts, seq, steps, stream, sampler, max_over_ranks, barrier,
+def bench_e2e(torch, brev, inputs, pts, seq, steps, stream, sampler, reduce_max, barrier,
               ws):
     """The sweep through brev_permute_host: pinned host input copied in,
     permuted, result copied back, every point every step."""
@@ -460,7 +492,7 @@ def bench_e2e(torch, brev, inputs, pts, seq, steps, stream, sampler, max_over_ra
     for _ in range(steps):
         step()
     barrier()
-    el = max_over_ranks(time.perf_counter() - t0)
+    el = reduce_max(time.perf_counter() - t0)
     sampler.window(w0, time.time())
     step_bytes = sum(p["bytes"] for p, _ in seq)
     return {"value": round(ws * step_bytes * steps / el / 1e9, 1), "unit": "GB/s",
@@ -525,7 +557,7 @@ def run_reference(args):
     if rank != 0:
         return
     # size each step so that the whole run stays within about 90 s
-    budget = max(0.05, 90.0 / max(1, args.steps + args.warmup))
+    budget = max(0.02, args.ref_seconds / max(1, args.steps + args.warmup))
     kmax, pts = largest_k_within(budget)
     for _ in range(args.warmup):
         time_oracle(pts)

@@ -190,6 +190,8 @@ struct Choice {
   const ShapeEntry* entry;
 };
 
+static Choice choose_default(int k, int E, bool inplace, bool vec16);
+
 static Choice choose(int k, int E, bool inplace, bool vec16) {
   const int bmin = b_min_for(E);
   if (k < 2 * bmin) return {true, nullptr};
@@ -200,6 +202,14 @@ static Choice choose(int k, int E, bool inplace, bool vec16) {
     if (t[0] > 0 && t[1] > 0 && t[0] + t[1] <= k)
       if (const ShapeEntry* s = find_shape(E, 16, t[0], t[1], kind)) return {false, s};
   }
+  return choose_default(k, E, inplace, vec16);
+}
+
+// The built-in shape, ignoring the tuned table.
+static Choice choose_default(int k, int E, bool inplace, bool vec16) {
+  const int bmin = b_min_for(E);
+  if (k < 2 * bmin) return {true, nullptr};
+  const int kind = inplace ? 1 : 0;
   const int W = vec16 ? 16 : E;
   for (int b = std::min(default_b(E, inplace), k / 2); b >= bmin; --b)
     if (const ShapeEntry* s = find_shape(E, W, b, b, kind)) return {false, s};
@@ -604,8 +614,9 @@ brev_status brev_autotune(int k_min, int k_max, int elem_bytes, const char* cach
       for (int ip = 0; ip < 2 && result == BREV_OK; ++ip) {
         int n = 0;
         const ShapeEntry* t = table_for(E, &n);
-        double best = 1e30;
+        double best = 1e30, def_med = 0;
         int bbx = 0, bbz = 0;
+        const ShapeEntry* def = choose_default(k, E, ip != 0, true).entry;
         for (int i = 0; i < n; ++i) {
           if (t[i].E != E || t[i].W != 16 || t[i].kind != ip || t[i].bx + t[i].bz > k) continue;
           Choice c{false, &t[i]};
@@ -627,11 +638,20 @@ brev_status brev_autotune(int k_min, int k_max, int elem_bytes, const char* cach
           if (result != BREV_OK) break;
           std::sort(ms.begin(), ms.end());
           const double med = ms[ms.size() / 2];
+          if (&t[i] == def) def_med = med;
           if (med < best) {
             best = med;
             bbx = t[i].bx;
             bbz = t[i].bz;
           }
+        }
+        // keep the built-in shape unless another one is clearly faster:
+        // small arrays are launch-latency bound and their timings differ
+        // by noise only
+        if (def && def_med > 0 && best > 0.97 * def_med) {
+          best = def_med;
+          bbx = def->bx;
+          bbz = def->bz;
         }
         if (bbx > 0) {
           std::lock_guard<std::mutex> lk(g_mu);

@@ -33,6 +33,12 @@ struct BatchDesc {
 };
 
 constexpr int BATCH_THREADS = 256;
+#ifndef BREV_BATCHED_MIN_CTAS
+#define BREV_BATCHED_MIN_CTAS 3  // register cap: 65536 / (256 * 3) = 85 per thread
+#endif
+#ifndef BREV_BATCHED_BODY_ATTR
+#define BREV_BATCHED_BODY_ATTR __noinline__
+#endif
 
 // Last descriptor whose first_ticket <= t (descriptors sorted by
 // first_ticket, strictly increasing, first one 0).  Run by one full warp:
@@ -56,58 +62,53 @@ __device__ __forceinline__ int find_array(const BatchDesc* __restrict__ d, int c
   return lo;
 }
 
-template <int E, int B>
-__device__ __forceinline__ void run_tile_unit(const BatchDesc& d, unsigned u, uint4* sm) {
-  using G = Geom<E, 16, B, B>;
-  tile_inplace_body<G, BATCH_THREADS>(d.ptr, d.k, u, reinterpret_cast<uint4*>(sm));
+// One body per element size with the tile exponent at run time, each a
+// separate (not inlined) function: the kernel's register count is then that
+// of the largest body, not of all bodies inlined side by side.
+template <int E>
+__device__ BREV_BATCHED_BODY_ATTR void run_tiles(char* ptr, int k, int b, unsigned u, uint4* sm) {
+  tile_inplace_body_rt<E, BATCH_THREADS>(ptr, k, b, u, sm);
+}
+
+template <int E>
+__device__ BREV_BATCHED_BODY_ATTR void run_small(char* ptr, int k, uint4* sm) {
+  small_body<E>(ptr, ptr, k, BATCH_THREADS, reinterpret_cast<typename ChunkT<E>::type*>(sm));
 }
 
 __device__ __forceinline__ void run_unit(const BatchDesc& d, unsigned u, uint4* sm) {
+  if (d.b == 0) {
+    switch (d.E) {
+      case 16: run_small<16>(d.ptr, d.k, sm); break;
+      case 8: run_small<8>(d.ptr, d.k, sm); break;
+      case 4: run_small<4>(d.ptr, d.k, sm); break;
+    }
+    return;
+  }
   switch (d.E) {
-    case 16:
-      switch (d.b) {
-        case 0: small_body<16>(d.ptr, d.ptr, d.k, BATCH_THREADS, sm); break;
-        case 3: run_tile_unit<16, 3>(d, u, sm); break;
-        case 4: run_tile_unit<16, 4>(d, u, sm); break;
-        case 5: run_tile_unit<16, 5>(d, u, sm); break;
-        case 6: run_tile_unit<16, 6>(d, u, sm); break;
-      }
-      break;
-    case 8:
-      switch (d.b) {
-        case 0: small_body<8>(d.ptr, d.ptr, d.k, BATCH_THREADS, reinterpret_cast<uint2*>(sm)); break;
-        case 4: run_tile_unit<8, 4>(d, u, sm); break;
-        case 5: run_tile_unit<8, 5>(d, u, sm); break;
-        case 6: run_tile_unit<8, 6>(d, u, sm); break;
-      }
-      break;
-    case 4:
-      switch (d.b) {
-        case 0: small_body<4>(d.ptr, d.ptr, d.k, BATCH_THREADS, reinterpret_cast<uint32_t*>(sm)); break;
-        case 5: run_tile_unit<4, 5>(d, u, sm); break;
-        case 6: run_tile_unit<4, 6>(d, u, sm); break;
-        case 7: run_tile_unit<4, 7>(d, u, sm); break;
-      }
-      break;
+    case 16: run_tiles<16>(d.ptr, d.k, d.b, u, sm); break;
+    case 8: run_tiles<8>(d.ptr, d.k, d.b, u, sm); break;
+    case 4: run_tiles<4>(d.ptr, d.k, d.b, u, sm); break;
   }
 }
 
-__global__ void __launch_bounds__(BATCH_THREADS)
+__global__ void __launch_bounds__(BATCH_THREADS, BREV_BATCHED_MIN_CTAS)
     k_batched(const BatchDesc* __restrict__ desc, int count, unsigned long long tickets,
               unsigned long long* ticket_ctr) {
   extern __shared__ uint4 smem_u4[];
-  __shared__ unsigned long long s_ticket;
+  __shared__ unsigned long long s_next;
   __shared__ int s_array;
-  for (;;) {
-    if (threadIdx.x == 0) s_ticket = atomicAdd(ticket_ctr, 1ull);
-    __syncthreads();
-    const unsigned long long t = s_ticket;
-    if (t >= tickets) return;
+  if (threadIdx.x == 0) s_next = atomicAdd(ticket_ctr, 1ull);
+  __syncthreads();
+  unsigned long long t = s_next;
+  while (t < tickets) {
     if (threadIdx.x < 32) {
       const int a = find_array(desc, count, t);
       if (threadIdx.x == 0) s_array = a;
     }
-    __syncthreads();
+    __syncthreads();  // s_array written; every thread has read s_next (= t)
+    // take the next ticket now: the atomic's round trip overlaps this
+    // ticket's units (its value is read after their barriers)
+    if (threadIdx.x == 0) s_next = atomicAdd(ticket_ctr, 1ull);
     const BatchDesc d = desc[s_array];
     const unsigned first = (unsigned)(t - d.first_ticket) * d.grain;
     const unsigned last = min(first + d.grain, d.units);
@@ -115,29 +116,34 @@ __global__ void __launch_bounds__(BATCH_THREADS)
       run_unit(d, u, smem_u4);
       __syncthreads();  // the next unit reuses the shared-memory tiles
     }
+    t = s_next;  // written before the barrier that ended the last unit
   }
 }
 
 // ------------------------------------------------------------------ host --
 
+// Tile exponents with a body in run_unit (at most 16 KiB tiles, so the
+// kernel keeps several CTAs per SM).
 static bool batched_shape_ok(int E, int b) {
   switch (E) {
-    case 16: return b == 0 || (b >= 3 && b <= 6);
-    case 8: return b == 0 || (b >= 4 && b <= 6);
-    case 4: return b == 0 || (b >= 5 && b <= 7);
+    case 16: return b == 0 || (b >= 3 && b <= 5);
+    case 8: return b == 0 || (b >= 4 && b <= 5);
+    case 4: return b == 0 || (b >= 5 && b <= 6);
   }
   return false;
 }
 
-// Tile exponent for an in-place array in the batched kernel: the tuned or
-// default in-place shape of the single-array path, clamped to the bodies
-// compiled in above; 0 for arrays staged whole.
+// Tile exponent for an in-place array in the batched kernel.  Every body
+// runs with 256 threads, so the tile should give each thread several
+// 16-byte chunks: 16 KiB tiles with 256-512-byte rows (E=16: b=5, E=8:
+// b=5, E=4: b=6), smaller only when the array is too short for them; 0
+// stages the whole array in one CTA (k < 2 b_min).
 static int batched_b(int k, int E) {
-  int bx = 0, bz = 0;
-  if (brev_tile_shape(k, E, 1, &bx, &bz) != BREV_OK) return -1;
-  if (bx == 0) return 0;
-  if (!batched_shape_ok(E, bx)) return -1;
-  return bx;
+  const int bmin = b_min_for(E);
+  if (k < 2 * bmin) return 0;
+  const int pref = E == 16 ? 5 : (E == 8 ? 5 : 6);
+  const int b = std::min(pref, k / 2);
+  return batched_shape_ok(E, b) ? b : -1;
 }
 
 struct BatchPlanData {
@@ -179,8 +185,8 @@ static brev_status build_batch(const BatchItem* items, int count, BatchPlanData*
       unit_bytes = 2ull * ((unsigned long long)it.E << (2 * b));
       out->smem = std::max<unsigned>(out->smem, (unsigned)unit_bytes);
     }
-    // about 64 KiB of tile data per ticket
-    const unsigned long long g = std::max<unsigned long long>(1, 65536ull / unit_bytes);
+    // about 256 KiB of tile data per ticket
+    const unsigned long long g = std::max<unsigned long long>(1, 262144ull / unit_bytes);
     d.grain = (unsigned)std::min<unsigned long long>(g, d.units);
     tmp.push_back({d, (unsigned long long)it.E << it.k});
   }
@@ -487,7 +493,7 @@ extern "C" brev_status brev_permute_batched_noalloc(void* const* ptr_array,
       unit_bytes = 2ull * ((unsigned long long)it.E << (2 * b));
     }
     smem = std::max<unsigned>(smem, (unsigned)unit_bytes);
-    const unsigned long long g = std::max<unsigned long long>(1, 65536ull / unit_bytes);
+    const unsigned long long g = std::max<unsigned long long>(1, 262144ull / unit_bytes);
     d.grain = (unsigned)std::min<unsigned long long>(g, d.units);
     h.desc[nd] = d;
     h.bytes[nd] = (unsigned long long)it.E << it.k;

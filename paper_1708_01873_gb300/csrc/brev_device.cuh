@@ -186,7 +186,7 @@ __device__ __forceinline__ void xpose(const typename ChunkT<W>::type (&in)[W / E
 }
 
 // ---------------------------------------------------------- geometry --
-constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v / 2); }
+__host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v / 2); }
 
 template <int E_, int W_, int BX_, int BZ_>
 struct Geom {
@@ -323,6 +323,104 @@ __device__ __forceinline__ void tile_inplace_body(char* data, int k, uint32_t q,
   __syncthreads();
   store_tile<G, NTHR>(sm, tr, stride);  // tile y's elements land in tile rev(y)
   if (nt == 2) store_tile<G, NTHR>(sm + G::CHUNKS, ty, stride);
+}
+
+// ------------------------------------------- runtime-geometry bodies --
+// The same square tile (16-byte path) with the exponent b a runtime value,
+// for the batched kernel, where one CTA meets many tile sizes: one body per
+// element size instead of one per (E, b).  Same shared-memory layout and
+// swizzle as Geom<E, 16, b, b>; NTHR threads; b >= b_min(E).
+constexpr int RT_BATCH = 4;  // loads in flight per thread per batch
+
+template <int E, int NTHR>
+__device__ __forceinline__ void load_tiles_rt(uint4* sm, const char* src0, const char* src1,
+                                              uint64_t row_stride, int nt, int b) {
+  constexpr int V = 16 / E;
+  constexpr int LOG_V = ilog2c(V);
+  const int log_cin = b - LOG_V;
+  const int chunks = 1 << (b + log_cin);
+  const int per = chunks >= NTHR ? chunks / NTHR : 1;
+  const int total = per * nt;
+  const int tid = threadIdx.x;
+#pragma unroll 1
+  for (int b0 = 0; b0 < total; b0 += RT_BATCH) {
+    uint4 r[RT_BATCH];
+#pragma unroll
+    for (int j = 0; j < RT_BATCH; ++j) {
+      const int f = b0 + j;
+      const int t = f / per, i = f - t * per;
+      const int q = tid + i * NTHR;
+      if (f < total && q < chunks) {
+        const int x = q >> log_cin, c = q & ((1 << log_cin) - 1);
+        r[j] = gload<16, false>((t == 0 ? src0 : src1) + (uint64_t)x * row_stride +
+                                (unsigned)c * 16);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < RT_BATCH; ++j) {
+      const int f = b0 + j;
+      const int t = f / per, i = f - t * per;
+      const int q = tid + i * NTHR;
+      if (f < total && q < chunks) {
+        const int x = q >> log_cin, c = q & ((1 << log_cin) - 1);
+        const int X = (int)rev_bits((uint32_t)x, b);
+        const int pc = c ^ ((X >> LOG_V) & 7);
+        sm[t * chunks + (X << log_cin) + pc] = r[j];
+      }
+    }
+  }
+}
+
+template <int E, int NTHR>
+__device__ __forceinline__ void store_tile_rt(const uint4* sm, char* dst_tile,
+                                              uint64_t row_stride, int b) {
+  constexpr int V = 16 / E;
+  constexpr int LOG_V = ilog2c(V);
+  const int log_cin = b - LOG_V;
+  const int units = 1 << (2 * log_cin);
+  const int tid = threadIdx.x;
+#pragma unroll 1
+  for (int u = tid; u < units; u += NTHR) {
+    const int c = u >> log_cin, d = u & ((1 << log_cin) - 1);
+    const int pc = c ^ (d & 7);
+    uint4 blk[V], out[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) blk[j] = sm[((d * V + j) << log_cin) + pc];
+    xpose<E, 16>(blk, out);
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      const uint32_t Z = rev_bits((uint32_t)(c * V + e), b);
+      gstore<16>(dst_tile + (uint64_t)Z * row_stride + (unsigned)d * 16, out[e]);
+    }
+  }
+}
+
+// In-place unit q of a 2^k-element array with square tiles of runtime b
+// (pairs first, then self-paired tiles; as tile_inplace_body).
+template <int E, int NTHR>
+__device__ __forceinline__ void tile_inplace_body_rt(char* data, int k, int b, uint32_t q,
+                                                     uint4* sm) {
+  const int wy = k - 2 * b;
+  const uint32_t npairs = count_lt(wy);
+  uint32_t y, ry;
+  int nt;
+  if (q < npairs) {
+    y = unrank_lt(q, wy);
+    ry = rev_bits(y, wy);
+    nt = 2;
+  } else {
+    y = unrank_self(q - npairs, wy);
+    ry = y;
+    nt = 1;
+  }
+  const uint64_t stride = (uint64_t)E << (k - b);
+  char* const ty = data + ((uint64_t)y << b) * E;
+  char* const tr = data + ((uint64_t)ry << b) * E;
+  load_tiles_rt<E, NTHR>(sm, ty, tr, stride, nt, b);
+  __syncthreads();
+  store_tile_rt<E, NTHR>(sm, tr, stride, b);
+  constexpr int LOG_V = ilog2c(16 / E);
+  if (nt == 2) store_tile_rt<E, NTHR>(sm + (1 << (2 * b - LOG_V)), ty, stride, b);
 }
 
 // Whole array staged in one CTA (small arrays): element i is written to
