@@ -45,6 +45,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="brev", choices=["brev", "reference"])
     ap.add_argument("--kmax", type=int, default=28, help="largest k of the sweep")
+    ap.add_argument("--kinds", default="u32,f32,c64,c128",
+                    help="element kinds of the sweep (comma separated)")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -53,6 +55,8 @@ def parse_args():
     ap.add_argument("--ref-seconds", type=float, default=90.0,
                     help="total oracle time budget of --impl reference")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--batch-kmax", type=int, default=20)
     ap.add_argument("--no-serve", action="store_true")
     return ap.parse_args()
 
@@ -160,9 +164,11 @@ def shape_name(brev, k, E, inplace):
 
 
 # ------------------------------------------------------------ the sweep --
-def make_sweep(torch, inputs, kmax, device):
+def make_sweep(torch, inputs, kmax, device, kinds=None):
     pts = []
     for kind, E in SWEEP_KINDS:
+        if kinds and kind not in kinds:
+            continue
         for k in range(SWEEP_KS[0], kmax + 1):
             n = 1 << k
             src = torch.empty(n * E, dtype=torch.uint8, device=device)
@@ -216,7 +222,7 @@ def run_brev(args):
     def reduce_max(x):
         return max_over_ranks(x, ws, device)
 
-    pts = make_sweep(torch, inputs, args.kmax, device)
+    pts = make_sweep(torch, inputs, args.kmax, device, args.kinds.split(","))
     seq = sweep_order(pts)
     step_bytes = sum(p["bytes"] for p, _ in seq)
     names = [shape_name(brev, p["k"], p["E"], ip) for p, ip in seq]
@@ -260,42 +266,44 @@ def run_brev(args):
     # per-kernel aggregates from the per-launch events
     per_kernel = {}
     per_point = {}
-    for s in range(args.steps):
-        for i, ((p, ip), (ea, eb)) in enumerate(zip(seq, evs[s])):
+    for s_ in range(args.steps):
+        for i, ((p, ip), (ea, eb)) in enumerate(zip(seq, evs[s_])):
             ms = ea.elapsed_time(eb)
-            d = per_kernel.setdefault(names[i], {"ms": 0.0, "bytes": 0, "launches": 0})
-            d["ms"] += ms
-            d["bytes"] += p["bytes"]
-            d["launches"] += 1
+            per_kernel[names[i]] = per_kernel.get(names[i], 0.0) + ms
             key = f"{p['kind']}_{'ip' if ip else 'oop'}_k{p['k']}"
-            per_point.setdefault(key, []).append(ms)
-    dom_name = max(per_kernel, key=lambda n: per_kernel[n]["ms"])
-    dom = per_kernel[dom_name]
-    achieved = dom["bytes"] / (dom["ms"] * 1e-3) / 1e9
-    total_kernel_ms = sum(d["ms"] for d in per_kernel.values())
-    traffic = load_traffic(dom_name)
+            per_point.setdefault(key, {"ms": [], "bytes": p["bytes"], "k": p["k"], "E": p["E"],
+                                       "mode": "ip" if ip else "oop", "kernel": names[i]})
+            per_point[key]["ms"].append(ms)
+    total_kernel_ms = sum(per_kernel.values())
+    # dominant kernel = most device time; its roofline is read at its
+    # largest launch configuration (one fixed size per launch)
+    dom_name = max(per_kernel, key=per_kernel.get)
+    dom_pts = [v for v in per_point.values() if v["kernel"] == dom_name]
+    dom = max(dom_pts, key=lambda v: (v["k"], sum(v["ms"])))
+    dom_ms = statistics.mean(dom["ms"])
+    achieved = dom["bytes"] / (dom_ms * 1e-3) / 1e9
+    traffic = load_traffic(dom_name, dom["k"], dom["E"], dom["mode"])
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
-                "kernel": dom_name, "peak_source": f"{peak_src} (copy bandwidth)",
-                "share_of_step": round(dom["ms"] / total_kernel_ms, 3),
-                "launches_per_step": dom["launches"] // args.steps,
-                "bytes_per_launch": dom["bytes"] // dom["launches"],
+                "kernel": dom_name,
+                "launch": f"k={dom['k']} E={dom['E']} {dom['mode']}",
+                "bytes_per_launch": dom["bytes"],
+                "avg_launch_ms": round(dom_ms, 4),
+                "launches_timed": len(dom["ms"]),
+                "peak_source": f"{peak_src} (copy bandwidth)",
+                "kernel_share_of_step": round(per_kernel[dom_name] / total_kernel_ms, 3),
                 "nominal_gbs": round(info["nominal_gbs"], 1),
                 "frac_nominal": round(achieved / info["nominal_gbs"], 4)}
     large = {}
     for key, v in per_point.items():
-        k = int(key.rsplit("k", 1)[1])
-        if k >= 26:
-            kind = key.split("_")[0]
-            E = dict(SWEEP_KINDS)[kind]
-            med = statistics.median(v)
-            large[key] = round(2 * (1 << k) * E / (med * 1e-3) / 1e9, 1)
+        if v["k"] >= 26:
+            large[key] = round(v["bytes"] / (statistics.median(v["ms"]) * 1e-3) / 1e9, 1)
 
     # ---------------------------------------------------- batched (cfg 4)
     batched = None
     if not args.no_batched:
         batched = bench_batched(torch, brev, inputs, device, stream, sampler, reduce_max,
-                                barrier)
+                                barrier, count=args.batch_count, kmax=args.batch_kmax)
 
     # ------------------------------------------------------------ e2e
     e2e = None
@@ -359,36 +367,41 @@ def run_brev(args):
         dist.destroy_process_group()
 
 
-def load_traffic(kernel_name):
-    """dram read+write bytes per launch of ``kernel_name`` from the committed
-    ncu summary, if it was taken on the current kernel source."""
+def kernel_source_hash() -> str:
+    """Hash of the tile-kernel sources; a recorded ncu traffic figure is
+    used only while it matches."""
     import hashlib
+    h = hashlib.sha256()
+    for f in ("brev_device.cuh", "brev_kernels.cuh"):
+        with open(os.path.join(ROOT, "paper_1708_01873_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic(kernel_name, k, E, mode):
+    """DRAM read + write bytes of one launch of ``kernel_name`` at (k, E,
+    mode), from profiles/traffic.txt (an ncu capture of that launch), or
+    None if none was taken on the current kernel source."""
     p = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(p):
         return None
-    src_hash = hashlib.sha256()
-    for f in ("brev_device.cuh", "brev_kernels.cuh"):
-        with open(os.path.join(ROOT, "paper_1708_01873_gb300", "csrc", f), "rb") as fh:
-            src_hash.update(fh.read())
-    h = src_hash.hexdigest()[:16]
+    h = kernel_source_hash()
     with open(p) as fh:
         for line in fh:
             parts = line.split()
-            # kernel  source_hash  dram_bytes_per_launch  ...
-            if len(parts) >= 3 and parts[0] == kernel_name and parts[1] == h:
-                try:
-                    return int(float(parts[2]))
-                except ValueError:
-                    return None
+            # kernel k E mode source_hash dram_read dram_write
+            if (len(parts) >= 7 and not line.startswith("#") and parts[0] == kernel_name
+                    and parts[1] == str(k) and parts[2] == str(E) and parts[3] == mode
+                    and parts[4] == h):
+                return int(float(parts[5]) + float(parts[6]))
     return None
 
 
 def bench_batched(torch, brev, inputs, device, stream, sampler, reduce_max, barrier,
-                  reps=10, warm=3):
+                  reps=10, warm=3, count=4096, kmax=20):
     import numpy as np
     rng = np.random.default_rng(4)
-    count = 4096
-    ks = rng.integers(8, 21, size=count)
+    ks = rng.integers(8, kmax + 1, size=count)
     Es = rng.choice([8, 16], size=count)
     arrays = []
     for i in range(count):
@@ -445,8 +458,8 @@ def bench_batched(torch, brev, inputs, device, stream, sampler, reduce_max, barr
         ms = reduce_max(ea.elapsed_time(eb)) / reps
         out[name] = {"ms": round(ms, 3), "gbs": round(total / (ms * 1e-3) / 1e9, 1)}
     plan.close()
-    res = {"workload": "4096 arrays, k uniform in [8,20], E uniform in {8,16} (seed 4), "
-                       "in place; persistent = one launch per batch",
+    res = {"workload": f"{count} arrays, k uniform in [8,{kmax}], E uniform in {{8,16}} "
+                       "(seed 4), in place; persistent = one launch per batch",
            "bytes_per_batch": total, "launches_in_loop": int(loop_launches), **out,
            "speedup_persistent_graph_vs_loop": round(out["loop"]["ms"] /
                                                      out["persistent_graph"]["ms"], 2),

@@ -141,12 +141,14 @@ BREV_API brev_status brev_permute_batched_noalloc(void *const *ptr_array, const 
 
 /* ---------------------------------------------------------------- host path */
 
-/* End-to-end form for host buffers: copies src_host (2^log2n elements) to
- * a library-owned device workspace, permutes, and copies the result to
- * dst_host (which may equal src_host), all on `stream`, then waits for
- * the stream.  Pinned host memory gives the full link bandwidth; pageable
- * memory works but is slower.  The workspace is stream-ordered device
- * memory released back to the pool at the end of the call. */
+/* End-to-end form for host buffers: permutes src_host (2^log2n elements)
+ * into dst_host (which may equal src_host) on `stream`, then waits for the
+ * stream.  When both buffers are page-locked (cudaHostAlloc /
+ * cudaHostRegister) and the driver confirms that each whole range lies in
+ * its allocation, the tile kernel reads and writes the host memory
+ * directly over the CPU-GPU link (no device copy).  Otherwise the source is
+ * copied to stream-ordered device workspace, permuted there, and copied
+ * back.  The buffers must hold 2^log2n elements each. */
 BREV_API brev_status brev_permute_host(void *dst_host, const void *src_host, int log2n,
                               int elem_bytes, void *stream);
 

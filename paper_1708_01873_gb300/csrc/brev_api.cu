@@ -116,6 +116,47 @@ static AddrRangeFn address_range_fn() {
   return fn;
 }
 
+// cuPointerGetAttribute, looked up the same way.
+typedef int (*PtrAttrFn)(void* data, int attribute, unsigned long long ptr);
+static PtrAttrFn pointer_attribute_fn() {
+  static PtrAttrFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuPointerGetAttribute", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PtrAttrFn)p;
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+// [p, p + bytes) lies inside one page-locked host allocation that the
+// current device can address; *dev receives the device-side address of p.
+static bool pinned_host_range(const void* p, uint64_t bytes, void** dev) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer) return false;
+  PtrAttrFn f = pointer_attribute_fn();
+  if (!f) return false;
+  unsigned long long start = 0;
+  size_t size = 0;
+  const int kRangeStart = 11, kRangeSize = 12;  // CU_POINTER_ATTRIBUTE_RANGE_{START_ADDR,SIZE}
+  if (f(&start, kRangeStart, (unsigned long long)(uintptr_t)p) != 0 ||
+      f(&size, kRangeSize, (unsigned long long)(uintptr_t)p) != 0)
+    return false;
+  if ((unsigned long long)(uintptr_t)p < start ||
+      (unsigned long long)(uintptr_t)p + bytes > start + size)
+    return false;
+  *dev = a.devicePointer;
+  return true;
+}
+
 brev_status check_device_range(const void* p, uint64_t bytes, const char* what) {
   cudaPointerAttributes a;
   cudaError_t e = cudaPointerGetAttributes(&a, p);
@@ -405,6 +446,18 @@ brev_status brev_permute_host(void* dst_host, const void* src_host, int log2n, i
       return set_error(BREV_ERR_OVERLAP, "host source and destination overlap partially");
   }
   cudaStream_t st = (cudaStream_t)stream;
+  // Both buffers page-locked: the tile kernel reads the source and writes
+  // the result in host memory directly (over the coherent CPU-GPU link on
+  // Grace-Blackwell), both directions at once, with no device staging.
+  void *dsrc = nullptr, *ddst = nullptr;
+  if (pinned_host_range(src_host, bytes, &dsrc) && pinned_host_range(dst_host, bytes, &ddst)) {
+    s = launch_single(ddst, dsrc, log2n, elem_bytes, st);
+    if (s != BREV_OK) return s;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_error(e, "host-path synchronize");
+    return BREV_OK;
+  }
+  // Otherwise: copy in, permute in device memory, copy out.
   void* buf = nullptr;
   cudaError_t e = cudaMallocAsync(&buf, bytes, st);
   if (e != cudaSuccess) {
