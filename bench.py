@@ -157,10 +157,11 @@ class ClockSampler:
 
 
 def shape_name(brev, k, E, inplace):
-    bx, bz = brev.brev_tile_shape(k, E, inplace)
+    bx, bz, order = brev.brev_tile_shape(k, E, inplace)
     if bx == 0:
         return f"small_E{E}"
-    return f"tile_{'inplace' if inplace else 'oop'}_E{E}_{bx}x{bz}"
+    return (f"tile_{'inplace' if inplace else 'oop'}_E{E}_{bx}x{bz}"
+            + ("_blocked" if order == 1 else ""))
 
 
 # ------------------------------------------------------------ the sweep --

@@ -156,21 +156,27 @@ BREV_API brev_status brev_permute_host(void *dst_host, const void *src_host, int
 
 /* Tile shape used for (log2n, elem_bytes, in_place): bx high bits and bz
  * low bits per tile (the matrix-buffer side lengths 2^bx, 2^bz); bx = bz =
- * 0 means the whole array is staged in one CTA (small arrays).  Host-only
- * query, no GPU needed. */
-BREV_API brev_status brev_tile_shape(int log2n, int elem_bytes, int in_place, int *bx, int *bz);
+ * 0 means the whole array is staged in one CTA (small arrays).  order is
+ * the launch order of the tiles: 0 = tile y run by CTA y, 1 = blocked
+ * (consecutive CTAs take 8 x 8 blocks of (high, low) bits of y, so that
+ * both the tiles and their destinations come in runs of 8 adjacent tiles).
+ * Host-only query, no GPU needed. */
+BREV_API brev_status brev_tile_shape(int log2n, int elem_bytes, int in_place, int *bx, int *bz,
+                                     int *order);
 
-/* Run the permutation with a forced tile shape (tests and the tuner).
- * Out-of-place accepts bx != bz; in-place requires bx == bz.  Shapes that
- * are not compiled in return BREV_ERR_UNSUPPORTED.  src == dst means
- * in-place. */
+/* Run the permutation with a forced tile shape and launch order (tests and
+ * the tuner).  Out-of-place accepts bx != bz; in-place requires bx == bz.
+ * Shapes that are not compiled in return BREV_ERR_UNSUPPORTED.  src == dst
+ * means in-place. */
 BREV_API brev_status brev_permute_shape(void *dst, const void *src, int log2n, int elem_bytes,
-                               int bx, int bz, void *stream);
+                                        int bx, int bz, int order, void *stream);
 
-/* Number of compiled 16-byte-path tile shapes for (elem_bytes, in_place),
- * and the i-th one (host-only; the tuner's candidates). */
+/* Number of compiled 16-byte-path (tile shape, launch order) pairs for
+ * (elem_bytes, in_place), and the i-th one (host-only; the tuner's
+ * candidates). */
 BREV_API int brev_shape_count(int elem_bytes, int in_place);
-BREV_API brev_status brev_shape_at(int elem_bytes, int in_place, int i, int *bx, int *bz);
+BREV_API brev_status brev_shape_at(int elem_bytes, int in_place, int i, int *bx, int *bz,
+                                   int *order);
 
 /* Time every compiled shape for k in [k_min, k_max] (out-of-place and
  * in-place), keep the fastest in the library's table, and, if cache_path

@@ -46,10 +46,10 @@ SIGNATURES = {
     "brev_plan_launch": (_i, [_vp, _vp]),
     "brev_plan_destroy": (None, [_vp]),
     "brev_permute_host": (_i, [_vp, _vp, _i, _i, _vp]),
-    "brev_tile_shape": (_i, [_i, _i, _i, _ip, _ip]),
-    "brev_permute_shape": (_i, [_vp, _vp, _i, _i, _i, _i, _vp]),
+    "brev_tile_shape": (_i, [_i, _i, _i, _ip, _ip, _ip]),
+    "brev_permute_shape": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _vp]),
     "brev_shape_count": (_i, [_i, _i]),
-    "brev_shape_at": (_i, [_i, _i, _i, _ip, _ip]),
+    "brev_shape_at": (_i, [_i, _i, _i, _ip, _ip, _ip]),
     "brev_autotune": (_i, [_i, _i, _i, _cp]),
     "brev_load_tune_cache": (_i, [_cp]),
     "brev_reset_tuning": (None, []),
@@ -152,12 +152,13 @@ def brev_permute(data, in_place: bool = True, stream=None) -> None:
                               _stream_handle(stream, data.device)), "brev_permute")
 
 
-def brev_permute_shape(dst, src, bx: int, bz: int, stream=None) -> None:
-    """Forced tile shape (2^bx x 2^bz; 0, 0 = whole array in one CTA)."""
+def brev_permute_shape(dst, src, bx: int, bz: int, order: int = 0, stream=None) -> None:
+    """Forced tile shape (2^bx x 2^bz; 0, 0 = whole array in one CTA) and
+    launch order (0 plain, 1 blocked)."""
     _flat(dst), _flat(src)
     k = _log2(src.numel())
     _check(lib().brev_permute_shape(dst.data_ptr(), src.data_ptr(), k, src.element_size(),
-                                    bx, bz, _stream_handle(stream, src.device)),
+                                    bx, bz, order, _stream_handle(stream, src.device)),
            "brev_permute_shape")
 
 
@@ -248,20 +249,22 @@ def brev_permute_host(dst, src, stream=None) -> None:
 
 
 # ------------------------------------------------------------ tuning --
-def brev_tile_shape(log2n: int, elem_bytes: int, in_place: bool) -> tuple[int, int]:
-    bx, bz = ctypes.c_int(), ctypes.c_int()
+def brev_tile_shape(log2n: int, elem_bytes: int, in_place: bool) -> tuple[int, int, int]:
+    """(bx, bz, order) the library uses; (0, 0, 0) = whole array in one CTA."""
+    bx, bz, order = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(lib().brev_tile_shape(log2n, elem_bytes, int(bool(in_place)), ctypes.byref(bx),
-                                 ctypes.byref(bz)), "brev_tile_shape")
-    return bx.value, bz.value
+                                 ctypes.byref(bz), ctypes.byref(order)), "brev_tile_shape")
+    return bx.value, bz.value, order.value
 
 
-def brev_shapes(elem_bytes: int, in_place: bool) -> list[tuple[int, int]]:
+def brev_shapes(elem_bytes: int, in_place: bool) -> list[tuple[int, int, int]]:
+    """Compiled 16-byte-path (bx, bz, order) triples."""
     out = []
     for i in range(lib().brev_shape_count(elem_bytes, int(bool(in_place)))):
-        bx, bz = ctypes.c_int(), ctypes.c_int()
+        bx, bz, order = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _check(lib().brev_shape_at(elem_bytes, int(bool(in_place)), i, ctypes.byref(bx),
-                                   ctypes.byref(bz)), "brev_shape_at")
-        out.append((bx.value, bz.value))
+                                   ctypes.byref(bz), ctypes.byref(order)), "brev_shape_at")
+        out.append((bx.value, bz.value, order.value))
     return out
 
 

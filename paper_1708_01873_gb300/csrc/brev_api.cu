@@ -200,11 +200,12 @@ static const ShapeEntry* table_for(int E, int* n) {
   return nullptr;
 }
 
-static const ShapeEntry* find_shape(int E, int W, int bx, int bz, int kind) {
+static const ShapeEntry* find_shape(int E, int W, int bx, int bz, int kind, int order = 0) {
   int n = 0;
   const ShapeEntry* t = table_for(E, &n);
   for (int i = 0; i < n; ++i)
-    if (t[i].E == E && t[i].W == W && t[i].bx == bx && t[i].bz == bz && t[i].kind == kind)
+    if (t[i].E == E && t[i].W == W && t[i].bx == bx && t[i].bz == bz && t[i].kind == kind &&
+        t[i].order == order)
       return &t[i];
   return nullptr;
 }
@@ -222,8 +223,8 @@ static int default_b(int E, bool inplace) {
   return 0;
 }
 
-// tuned (bx, bz) per element size, in-place flag and k; 0 = not tuned
-static int8_t g_tuned[5][2][BREV_MAX_LOG2N + 1][2];
+// tuned (bx, bz, order) per element size, in-place flag and k; bx = 0: not tuned
+static int8_t g_tuned[5][2][BREV_MAX_LOG2N + 1][3];
 static double g_tuned_gbs[5][2][BREV_MAX_LOG2N + 1];
 
 struct Choice {
@@ -241,7 +242,7 @@ static Choice choose(int k, int E, bool inplace, bool vec16) {
     std::lock_guard<std::mutex> lk(g_mu);
     const int8_t* t = g_tuned[e_index(E)][kind][k];
     if (t[0] > 0 && t[1] > 0 && t[0] + t[1] <= k)
-      if (const ShapeEntry* s = find_shape(E, 16, t[0], t[1], kind)) return {false, s};
+      if (const ShapeEntry* s = find_shape(E, 16, t[0], t[1], kind, t[2])) return {false, s};
   }
   return choose_default(k, E, inplace, vec16);
 }
@@ -378,7 +379,7 @@ brev_status brev_permute(void* data, int log2n, int elem_bytes, int in_place, vo
 }
 
 brev_status brev_permute_shape(void* dst, const void* src, int log2n, int elem_bytes, int bx,
-                               int bz, void* stream) {
+                               int bz, int order, void* stream) {
   brev_status s = check_pair(dst, src, log2n, elem_bytes);
   if (s != BREV_OK) return s;
   const bool inplace = dst == src;
@@ -394,10 +395,11 @@ brev_status brev_permute_shape(void* dst, const void* src, int log2n, int elem_b
       return set_error(BREV_ERR_INVALID_ARG, "tile %dx%d does not fit k=%d", bx, bz, log2n);
     if (inplace && bx != bz)
       return set_error(BREV_ERR_INVALID_ARG, "in-place needs a square tile");
-    c.entry = find_shape(elem_bytes, vec16 ? 16 : elem_bytes, bx, bz, inplace ? 1 : 0);
+    if (order != 0 && order != 1) return set_error(BREV_ERR_INVALID_ARG, "order=%d", order);
+    c.entry = find_shape(elem_bytes, vec16 ? 16 : elem_bytes, bx, bz, inplace ? 1 : 0, order);
     if (!c.entry)
-      return set_error(BREV_ERR_UNSUPPORTED, "tile %dx%d not compiled for E=%d (%s path)", bx, bz,
-                       elem_bytes, vec16 ? "16-byte" : "element-wide");
+      return set_error(BREV_ERR_UNSUPPORTED, "tile %dx%d order %d not compiled for E=%d (%s path)",
+                       bx, bz, order, elem_bytes, vec16 ? "16-byte" : "element-wide");
   }
   if (inplace && log2n <= 1) return BREV_OK;
   return launch_choice(c, dst, src, log2n, elem_bytes, (cudaStream_t)stream);
@@ -480,18 +482,20 @@ brev_status brev_permute_host(void* dst_host, const void* src_host, int log2n, i
   return BREV_OK;
 }
 
-brev_status brev_tile_shape(int log2n, int elem_bytes, int in_place, int* bx, int* bz) {
+brev_status brev_tile_shape(int log2n, int elem_bytes, int in_place, int* bx, int* bz,
+                            int* order) {
   brev_status s = check_common(log2n, elem_bytes);
   if (s != BREV_OK) return s;
-  if (!bx || !bz) return set_error(BREV_ERR_INVALID_ARG, "NULL output");
+  if (!bx || !bz || !order) return set_error(BREV_ERR_INVALID_ARG, "NULL output");
   Choice c = choose(log2n, elem_bytes, in_place != 0, true);
   if (c.small) {
-    *bx = *bz = 0;
+    *bx = *bz = *order = 0;
     return BREV_OK;
   }
   if (!c.entry) return set_error(BREV_ERR_UNSUPPORTED, "no tile shape");
   *bx = c.entry->bx;
   *bz = c.entry->bz;
+  *order = c.entry->order;
   return BREV_OK;
 }
 
@@ -504,16 +508,17 @@ int brev_shape_count(int elem_bytes, int in_place) {
   return c;
 }
 
-brev_status brev_shape_at(int elem_bytes, int in_place, int i, int* bx, int* bz) {
+brev_status brev_shape_at(int elem_bytes, int in_place, int i, int* bx, int* bz, int* order) {
   int n = 0, c = 0;
   const ShapeEntry* t = table_for(elem_bytes, &n);
   const int kind = in_place ? 1 : 0;
-  if (!bx || !bz) return set_error(BREV_ERR_INVALID_ARG, "NULL output");
+  if (!bx || !bz || !order) return set_error(BREV_ERR_INVALID_ARG, "NULL output");
   for (int j = 0; j < n; ++j)
     if (t[j].E == elem_bytes && t[j].W == 16 && t[j].kind == kind) {
       if (c == i) {
         *bx = t[j].bx;
         *bz = t[j].bz;
+        *order = t[j].order;
         return BREV_OK;
       }
       ++c;
@@ -556,8 +561,8 @@ static brev_status write_cache(const char* path) {
         const int8_t* t = g_tuned[ei][ip][k];
         if (t[0] <= 0) continue;
         fprintf(f, "%s\n  {\"elem_bytes\": %d, \"log2n\": %d, \"in_place\": %d, \"bx\": %d, "
-                   "\"bz\": %d, \"gbs\": %.1f}",
-                first ? "" : ",", Es[ei], k, ip, t[0], t[1], g_tuned_gbs[ei][ip][k]);
+                   "\"bz\": %d, \"order\": %d, \"gbs\": %.1f}",
+                first ? "" : ",", Es[ei], k, ip, t[0], t[1], t[2], g_tuned_gbs[ei][ip][k]);
         first = false;
       }
   fprintf(f, "\n]}\n");
@@ -617,15 +622,18 @@ brev_status brev_load_tune_cache(const char* path) {
   for (const char* p = strchr(ent, '{'); p; p = strchr(p, '{')) {
     const char* q = strchr(p, '}');
     if (!q) break;
-    long E = 0, k = -1, ip = -1, bx = 0, bz = 0;
+    long E = 0, k = -1, ip = -1, bx = 0, bz = 0, order = 0;
+    if (!json_int(p, q, "order", &order)) order = 0;  // tables written before orders existed
     if (json_int(p, q, "elem_bytes", &E) && json_int(p, q, "log2n", &k) &&
         json_int(p, q, "in_place", &ip) && json_int(p, q, "bx", &bx) &&
         json_int(p, q, "bz", &bz) && valid_E((int)E) && k >= 0 && k <= BREV_MAX_LOG2N &&
         (ip == 0 || ip == 1) && bx > 0 && bz > 0 && bx + bz <= k && (ip == 0 || bx == bz) &&
-        find_shape((int)E, 16, (int)bx, (int)bz, (int)ip)) {
+        (order == 0 || order == 1) &&
+        find_shape((int)E, 16, (int)bx, (int)bz, (int)ip, (int)order)) {
       int8_t* t = g_tuned[e_index((int)E)][ip][k];
       t[0] = (int8_t)bx;
       t[1] = (int8_t)bz;
+      t[2] = (int8_t)order;
       ++loaded;
     }
     p = q + 1;
@@ -668,7 +676,7 @@ brev_status brev_autotune(int k_min, int k_max, int elem_bytes, const char* cach
         int n = 0;
         const ShapeEntry* t = table_for(E, &n);
         double best = 1e30, def_med = 0;
-        int bbx = 0, bbz = 0;
+        int bbx = 0, bbz = 0, bord = 0;
         const ShapeEntry* def = choose_default(k, E, ip != 0, true).entry;
         for (int i = 0; i < n; ++i) {
           if (t[i].E != E || t[i].W != 16 || t[i].kind != ip || t[i].bx + t[i].bz > k) continue;
@@ -696,6 +704,7 @@ brev_status brev_autotune(int k_min, int k_max, int elem_bytes, const char* cach
             best = med;
             bbx = t[i].bx;
             bbz = t[i].bz;
+            bord = t[i].order;
           }
         }
         // keep the built-in shape unless another one is clearly faster:
@@ -705,11 +714,13 @@ brev_status brev_autotune(int k_min, int k_max, int elem_bytes, const char* cach
           best = def_med;
           bbx = def->bx;
           bbz = def->bz;
+          bord = def->order;
         }
         if (bbx > 0) {
           std::lock_guard<std::mutex> lk(g_mu);
           g_tuned[e_index(E)][ip][k][0] = (int8_t)bbx;
           g_tuned[e_index(E)][ip][k][1] = (int8_t)bbz;
+          g_tuned[e_index(E)][ip][k][2] = (int8_t)bord;
           g_tuned_gbs[e_index(E)][ip][k] = 2.0 * (double)bytes / (best * 1e-3) / 1e9;
         }
       }

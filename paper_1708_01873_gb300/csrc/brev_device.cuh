@@ -86,6 +86,56 @@ __device__ __forceinline__ uint32_t unrank_self(uint32_t p, int w) {
   return (p << lw) | rev_bits(p >> (a - lw), lw);
 }
 
+// ------------------------------------------------ blocked tile order --
+// A launch order in which 64 consecutive CTAs cover an 8 x 8 block of
+// (high 3 bits, low 3 bits) of y at one middle value.  Their tiles y form 8
+// runs of 8 adjacent tiles, and so do the partner tiles rev(y), because
+// reversal swaps the high and low fields.  HBM rows are then read and
+// written in runs of eight tiles rather than one tile at scattered places.
+// Needs w >= 6 bits of y; the tuner decides per shape whether it pays.
+constexpr int BLOCK_ORDER_MIN_W = 6;
+
+// Out-of-place: the t-th tile in blocked order (a bijection of [0, 2^w)).
+__device__ __forceinline__ uint32_t blocked_tile(uint32_t t, int w) {
+  const uint32_t lo = t & 7u, hi = (t >> 3) & 7u, mid = t >> 6;
+  return (hi << (w - 3)) | (mid << 3) | lo;
+}
+
+// In-place: unit q (0 <= q < count_lt(w) + count_self(w)) in blocked order,
+// giving a tile y and its partner ry (ry == y: self-paired).  The blocks are
+// the 2^(w-6) middle values m.  A middle with m < rev(m) pairs its whole
+// block with block rev(m): 64 pair units led from block m.  A palindromic
+// middle pairs its block with itself: (hi, lo) leads a pair when
+// hi < rev(lo) (28 units, lo-major) and is self-paired when hi = rev(lo)
+// (8 units).
+__device__ __forceinline__ void blocked_unit(uint32_t q, int w, uint32_t& y, uint32_t& ry) {
+  const int mw = w - 6;
+  const uint32_t full = count_lt(mw) << 6;
+  uint32_t mid, hi, lo;
+  if (q < full) {
+    mid = unrank_lt(q >> 6, mw);
+    hi = (q >> 3) & 7u;
+    lo = q & 7u;
+  } else {
+    const uint32_t q2 = q - full;
+    mid = unrank_self(q2 / 36u, mw);
+    uint32_t r = q2 % 36u;
+    if (r < 28u) {
+      lo = 0;
+      while (r >= rev_c<3>(lo)) {
+        r -= rev_c<3>(lo);
+        ++lo;
+      }
+      hi = r;
+    } else {
+      lo = r - 28u;
+      hi = rev_c<3>(lo);
+    }
+  }
+  y = (hi << (w - 3)) | (mid << 3) | lo;
+  ry = rev_bits(y, w);
+}
+
 // ------------------------------------------------------- chunk types --
 template <int W> struct ChunkT;
 template <> struct ChunkT<16> { using type = uint4; };
@@ -299,7 +349,7 @@ __device__ __forceinline__ void tile_oop_body(char* __restrict__ dst,
 // self-paired tiles y = rev(y).  Both tiles of a pair are read before
 // either is written (Introduction, in-place matrix buffer: swap through the
 // buffer; Listing 1: each pair swapped once).
-template <class G, int NTHR>
+template <class G, int NTHR, int ORDER = 0>
 __device__ __forceinline__ void tile_inplace_body(char* data, int k, uint32_t q,
                                                   typename ChunkT<G::W>::type* sm) {
   static_assert(G::BX == G::BZ, "in-place needs square tiles");
@@ -307,7 +357,10 @@ __device__ __forceinline__ void tile_inplace_body(char* data, int k, uint32_t q,
   const uint32_t npairs = count_lt(wy);
   uint32_t y, ry;
   int nt;
-  if (q < npairs) {
+  if (ORDER == 1 && wy >= BLOCK_ORDER_MIN_W) {
+    blocked_unit(q, wy, y, ry);
+    nt = y == ry ? 1 : 2;
+  } else if (q < npairs) {
     y = unrank_lt(q, wy);
     ry = rev_bits(y, wy);
     nt = 2;

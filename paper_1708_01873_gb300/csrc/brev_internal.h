@@ -15,6 +15,7 @@ struct ShapeEntry {
   int W;        // access width: 16 (vector path) or E (element-wide path)
   int bx, bz;   // tile = 2^bx source rows x 2^bz elements
   int kind;
+  int order;    // 0: tile y = CTA index; 1: blocked order (runs of 8 tiles)
   const void* kernel;
   unsigned smem;   // dynamic shared memory per CTA
   int threads;     // CTA size

@@ -3,11 +3,11 @@
 
 namespace brev {
 const ShapeEntry g_shapes_e21[] = {
-    BREV_OOP(2, 16, 6, 6), BREV_OOP(2, 16, 7, 7),
-    BREV_INP(2, 16, 6),    BREV_INP(2, 16, 7),
+    BREV_OOP2(2, 6, 6), BREV_OOP2(2, 7, 7),
+    BREV_INP2(2, 6),    BREV_INP2(2, 7),
     BREV_OOP(2, 2, 6, 6),  BREV_INP(2, 2, 6),
-    BREV_OOP(1, 16, 7, 7), BREV_OOP(1, 16, 8, 8),
-    BREV_INP(1, 16, 7),    BREV_INP(1, 16, 8),
+    BREV_OOP2(1, 7, 7), BREV_OOP2(1, 8, 8),
+    BREV_INP2(1, 7),    BREV_INP2(1, 8),
     BREV_OOP(1, 1, 7, 7),  BREV_INP(1, 1, 7),
 };
 const int g_shapes_e21_n = sizeof(g_shapes_e21) / sizeof(g_shapes_e21[0]);

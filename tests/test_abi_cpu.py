@@ -55,7 +55,7 @@ def test_argument_checks_before_any_device_call(brev_lib):
     assert L.brev_permute_batched(None, None, 0, 4, None) == 0  # empty batch
     assert L.brev_permute_batched_noalloc(None, None, None, 1025, None) == 1
     assert "exceeds" in brev_lib.brev_last_error()
-    assert L.brev_permute_shape(64, 64, 10, 8, 4, 5, None) == 1  # in place needs square
+    assert L.brev_permute_shape(64, 64, 10, 8, 4, 5, 0, None) == 1  # in place needs square
     assert L.brev_autotune(5, 3, 8, None) == 1
     assert L.brev_autotune(0, 10, 7, None) == 1
     h = ctypes.c_void_p()
@@ -69,23 +69,29 @@ def test_tile_shape_choice(brev_lib):
     for E in (16, 8, 4, 2, 1):
         for k in range(0, 35):
             for ip in (False, True):
-                bx, bz = brev_lib.brev_tile_shape(k, E, ip)
+                bx, bz, order = brev_lib.brev_tile_shape(k, E, ip)
                 if k < 2 * b_min[E]:
-                    assert (bx, bz) == (0, 0)   # whole array in one CTA
+                    assert (bx, bz, order) == (0, 0, 0)   # whole array in one CTA
                 else:
                     assert bx + bz <= k and bx >= b_min[E] and bz >= b_min[E]
                     assert (E << bz) >= 128 and (E << bx) >= 128
                     if ip:
                         assert bx == bz
-                    assert (bx, bz) in brev_lib.brev_shapes(E, ip)
+                    assert (bx, bz, order) in brev_lib.brev_shapes(E, ip)
     # defaults (no tuning): 512-byte rows for 16-byte elements at large k
-    assert brev_lib.brev_tile_shape(28, 16, False) == (5, 5)
+    assert brev_lib.brev_tile_shape(28, 16, False) == (5, 5, 0)
+    # every 16-byte shape is compiled in both launch orders
+    for E in (16, 8, 4, 2, 1):
+        for ip in (False, True):
+            shapes = brev_lib.brev_shapes(E, ip)
+            assert {(bx, bz, 1) for bx, bz, o in shapes if o == 0} == \
+                {s for s in shapes if s[2] == 1}
 
 
 def test_tune_cache_round_trip_host_only(brev_lib, tmp_path):
     p = tmp_path / "t.json"
     entries = [
-        {"elem_bytes": 8, "log2n": 20, "in_place": 0, "bx": 5, "bz": 6, "gbs": 1.0},
+        {"elem_bytes": 8, "log2n": 20, "in_place": 0, "bx": 5, "bz": 6, "order": 1, "gbs": 1.0},
         {"elem_bytes": 8, "log2n": 20, "in_place": 1, "bx": 4, "bz": 4, "gbs": 1.0},
         # invalid entries are ignored: non-square in place, shape not compiled,
         # tile larger than the array
@@ -97,13 +103,13 @@ def test_tune_cache_round_trip_host_only(brev_lib, tmp_path):
                              "entries": entries}))
     brev_lib.brev_reset_tuning()
     brev_lib.brev_load_tune_cache(str(p))
-    assert brev_lib.brev_tile_shape(20, 8, False) == (5, 6)
-    assert brev_lib.brev_tile_shape(20, 8, True) == (4, 4)
+    assert brev_lib.brev_tile_shape(20, 8, False) == (5, 6, 1)
+    assert brev_lib.brev_tile_shape(20, 8, True) == (4, 4, 0)   # no "order" key: plain
     brev_lib.brev_reset_tuning()
     d21 = brev_lib.brev_tile_shape(21, 8, True)
     brev_lib.brev_load_tune_cache(str(p))
     assert brev_lib.brev_tile_shape(21, 8, True) == d21
-    assert brev_lib.brev_tile_shape(9, 16, False) != (5, 5)
+    assert brev_lib.brev_tile_shape(9, 16, False)[:2] != (5, 5)
     brev_lib.brev_reset_tuning()
     with pytest.raises(brev_lib.BrevError):
         brev_lib.brev_load_tune_cache(str(tmp_path / "missing.json"))
@@ -113,5 +119,6 @@ def test_shipped_tune_cache_is_valid(brev_lib):
     d = json.load(open(brev_lib.DEFAULT_TUNE_CACHE))
     assert d["format"] == "brev-tune-1" and d["sm_count"] > 0
     for e in d["entries"]:
-        assert (e["bx"], e["bz"]) in brev_lib.brev_shapes(e["elem_bytes"], bool(e["in_place"]))
+        assert (e["bx"], e["bz"], e.get("order", 0)) in \
+            brev_lib.brev_shapes(e["elem_bytes"], bool(e["in_place"]))
         assert e["bx"] + e["bz"] <= e["log2n"]

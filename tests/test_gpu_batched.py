@@ -188,13 +188,14 @@ def test_autotune_and_cache(brev_lib, oracle_lib, cuda_device, tmp_path):
     d = json.load(open(path))
     assert d["sm_count"] > 0 and d["entries"]
     for e in d["entries"]:
-        assert (e["bx"], e["bz"]) in brev_lib.brev_shapes(e["elem_bytes"], e["in_place"])
+        assert (e["bx"], e["bz"], e["order"]) in \
+            brev_lib.brev_shapes(e["elem_bytes"], e["in_place"])
     brev_lib.brev_reset_tuning()
     brev_lib.brev_load_tune_cache(path)
     for e in d["entries"]:
         if e["elem_bytes"] == 8 and 12 <= e["log2n"] <= 16:
             assert brev_lib.brev_tile_shape(e["log2n"], 8, bool(e["in_place"])) == \
-                (e["bx"], e["bz"])
+                (e["bx"], e["bz"], e["order"])
     # tuned shapes give the same result
     for k in (12, 16):
         src = device_array(90 + k, k, 8)

@@ -59,20 +59,24 @@ def test_single_pointer_out_of_place(brev_lib, oracle_lib, cuda_device, E):
 @pytest.mark.parametrize("E", ES)
 def test_every_compiled_shape(brev_lib, oracle_lib, cuda_device, E):
     for inplace in (False, True):
-        for bx, bz in brev_lib.brev_shapes(E, inplace):
-            for k in sorted({bx + bz, bx + bz + 1, bx + bz + 2, bx + bz + 5, 19}):
+        for bx, bz, order in brev_lib.brev_shapes(E, inplace):
+            # both launch orders; the blocked one needs >= 6 middle bits,
+            # and odd middle widths exercise its palindromic blocks
+            for k in sorted({bx + bz, bx + bz + 1, bx + bz + 2, bx + bz + 5, bx + bz + 6,
+                             bx + bz + 7, 19}):
                 seed = 4000 + 97 * bx + 13 * bz + k
                 src = device_array(seed, k, E)
                 h = host_array(seed, k, E)
                 if inplace:
-                    brev_lib.brev_permute_shape(src, src, bx, bz)
+                    brev_lib.brev_permute_shape(src, src, bx, bz, order)
                     got = src
                 else:
                     got = torch.empty_like(src)
-                    brev_lib.brev_permute_shape(got, src, bx, bz)
+                    brev_lib.brev_permute_shape(got, src, bx, bz, order)
                 exp = oracle_lib.brev_oop(h, k, E)
                 assert_bytes_equal(to_bytes(got), exp, E,
-                                   f"shape {bx}x{bz} k={k} E={E} inplace={inplace}")
+                                   f"shape {bx}x{bz} order {order} k={k} E={E} "
+                                   f"inplace={inplace}")
 
 
 @pytest.mark.parametrize("E", (8, 4, 2, 1))
@@ -194,8 +198,9 @@ def test_error_statuses_launch_nothing(brev_lib, cuda_device):
     assert L.brev_permute_to(p + 8, p, 9, 8, None) == 3        # partial overlap
     cpu = torch.zeros(1 << 10, dtype=torch.int64)
     assert L.brev_permute_to(cpu.data_ptr(), cpu.data_ptr(), 10, 8, None) == 1  # host ptr
-    assert L.brev_permute_shape(p, p, 10, 8, 4, 5, None) == 1  # in-place needs square
-    assert L.brev_permute_shape(p, p, 10, 8, 9, 9, None) == 1  # tile larger than array
+    assert L.brev_permute_shape(p, p, 10, 8, 4, 5, 0, None) == 1  # in-place needs square
+    assert L.brev_permute_shape(p, p, 10, 8, 9, 9, 0, None) == 1  # tile larger than array
+    assert L.brev_permute_shape(p, p, 10, 8, 5, 5, 2, None) == 1  # no such order
     assert brev_lib.brev_launch_count() == c0
     with pytest.raises(brev_lib.BrevError) as ei:
         brev_lib.brev_permute_shape(t, t, 3, 3)                # 64 B rows: not compiled

@@ -57,6 +57,32 @@ def unrank_self(p, w):
     return (p << lw) | brev(p >> (a - lw), lw)
 
 
+def blocked_tile(t, w):
+    lo, hi, mid = t & 7, (t >> 3) & 7, t >> 6
+    return (hi << (w - 3)) | (mid << 3) | lo
+
+
+def blocked_unit(q, w):
+    mw = w - 6
+    full = count_lt(mw) << 6
+    if q < full:
+        mid, hi, lo = unrank_lt(q >> 6, mw), (q >> 3) & 7, q & 7
+    else:
+        q2 = q - full
+        mid, r = unrank_self(q2 // 36, mw), q2 % 36
+        if r < 28:
+            lo = 0
+            while r >= brev(lo, 3):
+                r -= brev(lo, 3)
+                lo += 1
+            hi = r
+        else:
+            lo = r - 28
+            hi = brev(lo, 3)
+    y = (hi << (w - 3)) | (mid << 3) | lo
+    return y, brev(y, w)
+
+
 class Geom:
     def __init__(self, E, W, BX, BZ):
         self.E, self.W, self.BX, self.BZ = E, W, BX, BZ
@@ -158,20 +184,22 @@ SHAPES = {
 WIDE = {8: [(4, 4), (5, 5)], 4: [(5, 5), (6, 6)], 2: [(6, 6)], 1: [(7, 7)]}
 
 
-def run_oop(E, W, bx, bz, k, nthr=None):
+def run_oop(E, W, bx, bz, k, nthr=None, order=0):
     G = Geom(E, W, bx, bz)
     nthr = nthr or G.THREADS
     n = 1 << k
     wy = k - bx - bz
     loads, stores, conflicts = [], [], []
-    for y in range(1 << wy):
+    for t in range(1 << wy):
+        y = blocked_tile(t, wy) if (order == 1 and wy >= 6) else t
+        assert 0 <= y < (1 << wy)
         ry = brev(y, wy)
         emulate_tile(G, k, nthr, [y << bz], [ry << bx], 1 << (k - bx), 1 << (k - bz), n,
                      loads, stores, conflicts)
     return G, loads, stores, conflicts
 
 
-def run_inplace(E, W, b, k, nthr=None):
+def run_inplace(E, W, b, k, nthr=None, order=0):
     G = Geom(E, W, b, b)
     nthr = nthr or G.THREADS
     n = 1 << k
@@ -180,7 +208,11 @@ def run_inplace(E, W, b, k, nthr=None):
     units = count_lt(w) + count_self(w)
     seen = set()
     for q in range(units):
-        if q < count_lt(w):
+        if order == 1 and w >= 6:
+            y, ry = blocked_unit(q, w)
+            assert 0 <= y < (1 << w) and ry == brev(y, w)
+            src, dst = ([y << b, ry << b], [ry << b, y << b]) if y != ry else ([y << b], [y << b])
+        elif q < count_lt(w):
             y = unrank_lt(q, w)
             ry = brev(y, w)
             assert y < ry
@@ -189,9 +221,10 @@ def run_inplace(E, W, b, k, nthr=None):
             y = unrank_self(q - count_lt(w), w)
             assert y == brev(y, w)
             src, dst = [y << b], [y << b]
-        assert y not in seen
-        seen.add(y)
-        seen.add(brev(y, w))
+        y0 = src[0] >> b
+        assert y0 not in seen and brev(y0, w) not in seen
+        seen.add(y0)
+        seen.add(brev(y0, w))
         emulate_tile(G, k, nthr, src, dst, 1 << (k - b), 1 << (k - b), n, loads, stores,
                      conflicts)
     assert len(seen) == 1 << w  # every tile covered exactly once
@@ -286,3 +319,30 @@ def test_batched_array_search():
         for t in list(range(0, min(total, 300))) + rng.integers(0, total, 300).tolist():
             a = find_array(first, int(t))
             assert first[a] <= t < (first[a + 1] if a + 1 < count else total)
+
+
+@pytest.mark.parametrize("E", (16, 8, 4))
+def test_blocked_order_index_math(E):
+    """The blocked launch order (runs of 8 adjacent tiles) is a bijection
+    of the tiles / units and keeps every access in bounds."""
+    b = {16: 3, 8: 4, 4: 5}[E]
+    for k in (2 * b + 6, 2 * b + 7, 2 * b + 8):
+        if (1 << k) > (1 << 17):
+            continue
+        G, loads, stores, conf = run_oop(E, 16, b, b, k, order=1)
+        check_result(k, loads, stores)
+        G, loads, stores, conf = run_inplace(E, 16, b, k, order=1)
+        check_result(k, loads, stores)
+        assert sum(conf) == 0
+
+
+def test_blocked_unit_covers_all_tiles_large_w():
+    for w in range(6, 17):
+        seen = set()
+        for q in range(count_lt(w) + count_self(w)):
+            y, ry = blocked_unit(q, w)
+            assert y not in seen and ry not in seen
+            seen.add(y)
+            seen.add(ry)
+        assert len(seen) == 1 << w
+        assert sorted({blocked_tile(t, w) for t in range(1 << w)}) == list(range(1 << w))
