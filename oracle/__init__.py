@@ -63,6 +63,12 @@ def lib() -> ctypes.CDLL:
             L.oracle_brev_oop_mt.restype = i32
             L.oracle_brev_gather.argtypes = [vp, vp, vp, i64, i32, i32]
             L.oracle_brev_gather.restype = i32
+            L.oracle_transpose.argtypes = [vp, vp, i32, i32, i32]
+            L.oracle_transpose.restype = i32
+            L.oracle_even_odd.argtypes = [vp, vp, i32, i32]
+            L.oracle_even_odd.restype = i32
+            L.oracle_perfect_shuffle.argtypes = [vp, vp, i32, i32]
+            L.oracle_perfect_shuffle.restype = i32
             _lib = L
     return _lib
 
@@ -122,3 +128,32 @@ def brev_gather(src: np.ndarray, idx: np.ndarray, k: int,
     if rc != 0:
         raise ValueError("oracle_brev_gather rejected its arguments")
     return out
+
+
+def transpose(src: np.ndarray, log2_rows: int, log2_cols: int, elem_bytes: int) -> np.ndarray:
+    """dst[j * 2^a + i] = src[i * 2^c + j] for a 2^a x 2^c matrix."""
+    s = _as_bytes(src)
+    assert s.size == (1 << (log2_rows + log2_cols)) * elem_bytes
+    d = np.empty_like(s)
+    if lib().oracle_transpose(d.ctypes.data, s.ctypes.data, log2_rows, log2_cols,
+                              elem_bytes) != 0:
+        raise ValueError("oracle_transpose rejected its arguments")
+    return d
+
+
+def even_odd(src: np.ndarray, k: int, elem_bytes: int) -> np.ndarray:
+    s = _as_bytes(src)
+    assert s.size == (1 << k) * elem_bytes
+    d = np.empty_like(s)
+    if lib().oracle_even_odd(d.ctypes.data, s.ctypes.data, k, elem_bytes) != 0:
+        raise ValueError("oracle_even_odd rejected its arguments")
+    return d
+
+
+def perfect_shuffle(src: np.ndarray, k: int, elem_bytes: int) -> np.ndarray:
+    s = _as_bytes(src)
+    assert s.size == (1 << k) * elem_bytes
+    d = np.empty_like(s)
+    if lib().oracle_perfect_shuffle(d.ctypes.data, s.ctypes.data, k, elem_bytes) != 0:
+        raise ValueError("oracle_perfect_shuffle rejected its arguments")
+    return d

@@ -164,3 +164,63 @@ int oracle_brev_gather(void *out, const void *src, const uint64_t *idx,
     }
     return 0;
 }
+
+/* Matrix transposition, element by element, from its definition. */
+int oracle_transpose(void *dst, const void *src, int log2_rows, int log2_cols,
+                     int elem_bytes)
+{
+    uint64_t R, C, i, j;
+    unsigned char *d = (unsigned char *)dst;
+    const unsigned char *s = (const unsigned char *)src;
+    if (log2_rows < 0 || log2_cols < 0 || bad_args(log2_rows + log2_cols, elem_bytes) ||
+        !dst || !src)
+        return -1;
+    R = (uint64_t)1 << log2_rows;
+    C = (uint64_t)1 << log2_cols;
+    for (i = 0; i < R; ++i)
+        for (j = 0; j < C; ++j)
+            memcpy(d + (j * R + i) * (uint64_t)elem_bytes,
+                   s + (i * C + j) * (uint64_t)elem_bytes, (size_t)elem_bytes);
+    return 0;
+}
+
+/* Even indices first, then odd ones (the Stockham even-odd step). */
+int oracle_even_odd(void *dst, const void *src, int k, int elem_bytes)
+{
+    uint64_t n, i, out = 0;
+    unsigned char *d = (unsigned char *)dst;
+    const unsigned char *s = (const unsigned char *)src;
+    if (bad_args(k, elem_bytes) || !dst || !src)
+        return -1;
+    n = (uint64_t)1 << k;
+    for (i = 0; i < n; i += 2)
+        memcpy(d + (out++) * (uint64_t)elem_bytes, s + i * (uint64_t)elem_bytes,
+               (size_t)elem_bytes);
+    for (i = 1; i < n; i += 2)
+        memcpy(d + (out++) * (uint64_t)elem_bytes, s + i * (uint64_t)elem_bytes,
+               (size_t)elem_bytes);
+    return 0;
+}
+
+/* A deck cut in half and the halves interleaved (faro shuffle). */
+int oracle_perfect_shuffle(void *dst, const void *src, int k, int elem_bytes)
+{
+    uint64_t n, h, i;
+    unsigned char *d = (unsigned char *)dst;
+    const unsigned char *s = (const unsigned char *)src;
+    if (bad_args(k, elem_bytes) || !dst || !src)
+        return -1;
+    n = (uint64_t)1 << k;
+    if (n == 1) {
+        memcpy(d, s, (size_t)elem_bytes);
+        return 0;
+    }
+    h = n / 2;
+    for (i = 0; i < h; ++i) {
+        memcpy(d + (2 * i) * (uint64_t)elem_bytes, s + i * (uint64_t)elem_bytes,
+               (size_t)elem_bytes);
+        memcpy(d + (2 * i + 1) * (uint64_t)elem_bytes, s + (h + i) * (uint64_t)elem_bytes,
+               (size_t)elem_bytes);
+    }
+    return 0;
+}

@@ -49,6 +49,22 @@ int oracle_brev_oop_mt(void *dst, const void *src, int k, int elem_bytes,
 int oracle_brev_gather(void *out, const void *src, const uint64_t *idx,
                        int64_t count, int k, int elem_bytes);
 
+/* Transposition of a row-major 2^a x 2^c matrix of elem_bytes elements:
+ * dst[j * 2^a + i] = src[i * 2^c + j] (Introduction: the even-odd step as a
+ * matrix transposition).  dst and src must not overlap.  Returns 0 or -1. */
+int oracle_transpose(void *dst, const void *src, int log2_rows, int log2_cols,
+                     int elem_bytes);
+
+/* Even-odd step of the Stockham auto-sort (Introduction): the elements at
+ * even indices, in order, followed by those at odd indices.  n = 2^k, k >= 1
+ * (k = 0 copies the single element).  Returns 0 or -1. */
+int oracle_even_odd(void *dst, const void *src, int k, int elem_bytes);
+
+/* Perfect (faro) shuffle, the inverse of the even-odd step (Introduction):
+ * the two halves interleaved, dst[2i] = src[i], dst[2i+1] = src[n/2 + i].
+ * Returns 0 or -1. */
+int oracle_perfect_shuffle(void *dst, const void *src, int k, int elem_bytes);
+
 #ifdef __cplusplus
 }
 #endif

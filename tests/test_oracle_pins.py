@@ -219,3 +219,61 @@ def test_pins_catch_planted_mistake(mutant):
         except AssertionError:
             caught += 1
     assert caught >= 1, f"no pin caught {mutant.__name__}"
+
+
+# ------------------------------------------------ transposition oracles --
+def test_even_odd_golden_on_c_oracle(oracle_lib):
+    """P2 on the C oracle: [0..7] -> [0,2,4,6,1,3,5,7] (Introduction)."""
+    g = pins.read_golden("even_odd_k3.txt")
+    exp = [int(x) for x in g["output"]]
+    for E in (1, 4, 16):
+        got = pins.decode_index(oracle_lib.even_odd(pins.index_elems(8, E), 3, E), E).tolist()
+        assert got == exp
+
+
+def test_transpose_matches_numpy(oracle_lib):
+    """A library routine as the pin: numpy's transpose of the matrix view."""
+    for a, c in ((0, 0), (0, 3), (3, 0), (1, 5), (5, 1), (4, 4), (6, 3), (2, 9)):
+        for E in (1, 4, 16):
+            x = pins.fingerprint_elems(1 << (a + c), E, salt=a * 10 + c)
+            exp = x.reshape(1 << a, 1 << c, E).transpose(1, 0, 2).reshape(-1)
+            assert np.array_equal(oracle_lib.transpose(x, a, c, E), exp), (a, c, E)
+
+
+def test_even_odd_is_half_by_two_transpose_and_shuffle_inverts(oracle_lib):
+    for k in range(1, 14):
+        for E in (4, 8):
+            x = pins.fingerprint_elems(1 << k, E, salt=k)
+            eo = oracle_lib.even_odd(x, k, E)
+            assert np.array_equal(eo, oracle_lib.transpose(x, k - 1, 1, E))
+            assert np.array_equal(oracle_lib.perfect_shuffle(eo, k, E), x)
+            assert np.array_equal(oracle_lib.perfect_shuffle(x, k, E),
+                                  oracle_lib.transpose(x, 1, k - 1, E))
+
+
+def test_stockham_recursion_with_c_even_odd(oracle_lib):
+    """P5 with the C even-odd step: even-odd, then each half recursively,
+    equals the bit-reversed permutation."""
+    def rec(x, k, E):
+        if k == 0:
+            return x.copy()
+        eo = oracle_lib.even_odd(x, k, E)
+        h = (1 << (k - 1)) * E
+        return np.concatenate([rec(eo[:h], k - 1, E), rec(eo[h:], k - 1, E)])
+    for k in range(0, 13):
+        x = pins.fingerprint_elems(1 << k, 8, salt=k)
+        assert np.array_equal(rec(x, k, 8), oracle_lib.brev_oop(x, k, 8))
+
+
+def test_recursive_method_with_c_transpose(oracle_lib):
+    """Methods, cache-oblivious recursive method: reverse every block, square
+    transpose, reverse every block again (even k), with the C transpose."""
+    for k in (2, 4, 6, 8, 10, 12):
+        h = k // 2
+        for E in (4, 16):
+            x = pins.fingerprint_elems(1 << k, E, salt=k)
+            s = 1 << h
+            blocks = [oracle_lib.brev_oop(x[r * s * E:(r + 1) * s * E], h, E) for r in range(s)]
+            t = oracle_lib.transpose(np.concatenate(blocks), h, h, E)
+            blocks = [oracle_lib.brev_oop(t[r * s * E:(r + 1) * s * E], h, E) for r in range(s)]
+            assert np.array_equal(np.concatenate(blocks), oracle_lib.brev_oop(x, k, E))
