@@ -58,6 +58,7 @@ def parse_args():
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--batch-kmax", type=int, default=20)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-next", action="store_true")
     return ap.parse_args()
 
 
@@ -306,6 +307,12 @@ def run_brev(args):
         batched = bench_batched(torch, brev, inputs, device, stream, sampler, reduce_max,
                                 barrier, count=args.batch_count, kmax=args.batch_kmax)
 
+    # -------------------------------------------- widened rows (NEXT)
+    next_rows = None
+    if not args.no_next:
+        next_rows = bench_next(torch, brev, inputs, device, stream, sampler, reduce_max,
+                               barrier, peak)
+
     # ------------------------------------------------------------ e2e
     e2e = None
     if not args.no_e2e:
@@ -357,6 +364,7 @@ def run_brev(args):
             "large_arrays_gbs": large,
             "batched": batched,
             "serving": serving,
+            "transpositions_and_recursive": next_rows,
             "e2e": e2e,
             "gpu_launches": int(launches),
             "clocks": clocks,
@@ -396,6 +404,55 @@ def load_traffic(kernel_name, k, E, mode):
                     and parts[4] == h):
                 return int(float(parts[5]) + float(parts[6]))
     return None
+
+
+def bench_next(torch, brev, inputs, device, stream, sampler, reduce_max, barrier, peak,
+               reps=5, warm=2):
+    """The widened rows: transpositions (square and narrow: the even-odd step
+    and the perfect shuffle) and the paper's recursive method (three passes)
+    against the one-pass tile kernel, all on 4 GiB arrays."""
+    L = brev.lib()
+    sh = stream.cuda_stream
+
+    def timed(fn):
+        for _ in range(warm):
+            fn()
+        barrier()
+        ea = torch.cuda.Event(enable_timing=True)
+        eb = torch.cuda.Event(enable_timing=True)
+        w0 = time.time()
+        ea.record(stream)
+        for _ in range(reps):
+            fn()
+        eb.record(stream)
+        barrier()
+        sampler.window(w0, time.time())
+        return reduce_max(ea.elapsed_time(eb)) / reps
+
+    out = {}
+    k, E = 28, 16
+    src = torch.empty((1 << k) * E, dtype=torch.uint8, device=device)
+    inputs.fill_torch(src, 28, "c128", chunk=1 << 26)
+    dst = torch.empty_like(src)
+    nbytes = 2 * src.numel()
+    for name, a, c in (("transpose_16384x16384_c128", 14, 14),
+                       ("even_odd_c128_k28", 27, 1), ("perfect_shuffle_c128_k28", 1, 27)):
+        ms = timed(lambda: L.brev_transpose(dst.data_ptr(), src.data_ptr(), a, c, E, sh))
+        out[name] = {"ms": round(ms, 4), "gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
+                     "frac": round(nbytes / (ms * 1e-3) / 1e9 / peak, 4)}
+    ms = timed(lambda: L.brev_transpose(dst.data_ptr(), dst.data_ptr(), 14, 14, E, sh))
+    out["transpose_in_place_16384x16384_c128"] = {
+        "ms": round(ms, 4), "gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
+        "frac": round(nbytes / (ms * 1e-3) / 1e9 / peak, 4)}
+    one = timed(lambda: L.brev_permute_to(dst.data_ptr(), dst.data_ptr(), k, E, sh))
+    rec = timed(lambda: L.brev_permute_recursive(dst.data_ptr(), k, E, sh))
+    out["recursive_vs_one_pass_c128_k28"] = {
+        "one_pass_ms": round(one, 4), "recursive_ms": round(rec, 4),
+        "ratio": round(rec / one, 3),
+        "one_pass_gbs": round(nbytes / (one * 1e-3) / 1e9, 1),
+        "recursive_hbm_passes": 3}
+    del src, dst
+    return out
 
 
 def bench_batched(torch, brev, inputs, device, stream, sampler, reduce_max, barrier,

@@ -139,6 +139,49 @@ BREV_API brev_status brev_permute_batched_noalloc(void *const *ptr_array, const 
                                                   const int *elem_bytes_array, int count,
                                                   void *stream);
 
+/* ---------------------------------------------------------------- transpositions */
+
+/* Transposition of a row-major 2^log2_rows x 2^log2_cols matrix of
+ * elem_bytes elements: dst[j * 2^log2_rows + i] = src[i * 2^log2_cols + j].
+ * The paper (Introduction) reads the Stockham even-odd step as such a
+ * transposition.  Same tile machinery as the permutation (staged through
+ * shared memory, whole rows moved in 16-byte vectors), with identity index
+ * maps.  dst == src is allowed for square matrices only (in place, tile
+ * pairs swapped); a non-square matrix in place returns
+ * BREV_ERR_UNSUPPORTED. */
+BREV_API brev_status brev_transpose(void *dst, const void *src, int log2_rows, int log2_cols,
+                                    int elem_bytes, void *stream);
+
+/* Even-odd step of the Stockham auto-sort (Introduction): the even-indexed
+ * elements in order, then the odd-indexed ones; the transposition of the
+ * n/2 x 2 matrix.  Out of place only (dst == src only for n <= 4). */
+BREV_API brev_status brev_even_odd(void *dst, const void *src, int log2n, int elem_bytes,
+                                   void *stream);
+
+/* Perfect (faro) shuffle, the inverse of the even-odd step: the two halves
+ * interleaved; the transposition of the 2 x n/2 matrix. */
+BREV_API brev_status brev_perfect_shuffle(void *dst, const void *src, int log2n,
+                                          int elem_bytes, void *stream);
+
+/* In-place bit reversal of each of 2^log2_segments contiguous segments of
+ * 2^log2_seglen elements (one launch for all segments).  The small,
+ * contiguous bit reversals of the paper's recursive method (Methods,
+ * cache-oblivious recursive bit-reversed permutation). */
+BREV_API brev_status brev_permute_segments(void *data, int log2_segments, int log2_seglen,
+                                           int elem_bytes, void *stream);
+
+/* The paper's recursive method with one level of recursion, in place, as a
+ * multi-pass comparison point for the one-pass tile kernel (Methods,
+ * cache-oblivious recursive bit-reversed permutation; Results, the GPU
+ * variant): for even k, index = x y with k/2 bits each, reverse every
+ * contiguous block (x rev(y)), transpose the square matrix (rev(y) x),
+ * reverse every block again (rev(y) rev(x)) -- three read+write passes.  Odd
+ * k takes the even-odd step first (Methods, odd number of bits) into
+ * stream-ordered device workspace, permutes each half, and copies back.
+ * Same result as brev_permute(data, log2n, elem_bytes, 1, stream). */
+BREV_API brev_status brev_permute_recursive(void *data, int log2n, int elem_bytes,
+                                            void *stream);
+
 /* ---------------------------------------------------------------- host path */
 
 /* End-to-end form for host buffers: permutes src_host (2^log2n elements)

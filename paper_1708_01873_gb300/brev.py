@@ -46,6 +46,11 @@ SIGNATURES = {
     "brev_plan_launch": (_i, [_vp, _vp]),
     "brev_plan_destroy": (None, [_vp]),
     "brev_permute_host": (_i, [_vp, _vp, _i, _i, _vp]),
+    "brev_transpose": (_i, [_vp, _vp, _i, _i, _i, _vp]),
+    "brev_even_odd": (_i, [_vp, _vp, _i, _i, _vp]),
+    "brev_perfect_shuffle": (_i, [_vp, _vp, _i, _i, _vp]),
+    "brev_permute_segments": (_i, [_vp, _i, _i, _i, _vp]),
+    "brev_permute_recursive": (_i, [_vp, _i, _i, _vp]),
     "brev_tile_shape": (_i, [_i, _i, _i, _ip, _ip, _ip]),
     "brev_permute_shape": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _vp]),
     "brev_shape_count": (_i, [_i, _i]),
@@ -234,6 +239,54 @@ class BrevPlan:
 
 def brev_plan_create(tensors: Iterable) -> BrevPlan:
     return BrevPlan(tensors)
+
+
+# ---------------------------------------------------- transpositions --
+def brev_transpose(dst, src, log2_rows: int, log2_cols: int, stream=None) -> None:
+    """dst (2^cols x 2^rows) = transpose of src (2^rows x 2^cols), both
+    flat and row-major; dst may be src for square matrices."""
+    _flat(dst), _flat(src)
+    if src.numel() != 1 << (log2_rows + log2_cols) or dst.numel() != src.numel():
+        raise ValueError("tensor sizes do not match the matrix shape")
+    _check(lib().brev_transpose(dst.data_ptr(), src.data_ptr(), log2_rows, log2_cols,
+                                src.element_size(), _stream_handle(stream, src.device)),
+           "brev_transpose")
+
+
+def brev_even_odd(dst, src, stream=None) -> None:
+    """Even-indexed elements, then odd-indexed ones (the Stockham step)."""
+    _flat(dst), _flat(src)
+    _check(lib().brev_even_odd(dst.data_ptr(), src.data_ptr(), _log2(src.numel()),
+                               src.element_size(), _stream_handle(stream, src.device)),
+           "brev_even_odd")
+
+
+def brev_perfect_shuffle(dst, src, stream=None) -> None:
+    """The two halves interleaved (inverse of brev_even_odd)."""
+    _flat(dst), _flat(src)
+    _check(lib().brev_perfect_shuffle(dst.data_ptr(), src.data_ptr(), _log2(src.numel()),
+                                      src.element_size(), _stream_handle(stream, src.device)),
+           "brev_perfect_shuffle")
+
+
+def brev_permute_segments(data, log2_segments: int, stream=None) -> None:
+    """Bit-reverse each of 2^log2_segments equal contiguous segments in place."""
+    _flat(data)
+    k = _log2(data.numel())
+    if log2_segments > k:
+        raise ValueError("more segments than elements")
+    _check(lib().brev_permute_segments(data.data_ptr(), log2_segments, k - log2_segments,
+                                       data.element_size(),
+                                       _stream_handle(stream, data.device)),
+           "brev_permute_segments")
+
+
+def brev_permute_recursive(data, stream=None) -> None:
+    """In-place permutation by the paper's recursive method (multi-pass)."""
+    _flat(data)
+    _check(lib().brev_permute_recursive(data.data_ptr(), _log2(data.numel()),
+                                        data.element_size(), _stream_handle(stream, data.device)),
+           "brev_permute_recursive")
 
 
 # -------------------------------------------------------------- host --

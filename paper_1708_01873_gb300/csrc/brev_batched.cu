@@ -67,7 +67,7 @@ __device__ __forceinline__ int find_array(const BatchDesc* __restrict__ d, int c
 // of the largest body, not of all bodies inlined side by side.
 template <int E>
 __device__ BREV_BATCHED_BODY_ATTR void run_tiles(char* ptr, int k, int b, unsigned u, uint4* sm) {
-  tile_inplace_body_rt<E, BATCH_THREADS>(ptr, k, b, u, sm);
+  tile_inplace_body_rt<E, 16, BATCH_THREADS>(ptr, k, b, u, sm);
 }
 
 template <int E>

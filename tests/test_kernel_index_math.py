@@ -346,3 +346,201 @@ def test_blocked_unit_covers_all_tiles_large_w():
             seen.add(ry)
         assert len(seen) == 1 << w
         assert sorted({blocked_tile(t, w) for t in range(1 << w)}) == list(range(1 << w))
+
+
+# ----------------------------------------------- runtime-geometry tiles --
+def emulate_g(E, W, nthr, rev, srcs, dsts, stride_in, stride_out, bx, bz, n, loads, stores):
+    """load_tiles_g / store_tile_g of one CTA (run-time bx, bz; rev maps on
+    or off).  srcs/dsts: element offsets of the tiles' corners."""
+    V = W // E
+    lv = V.bit_length() - 1
+    phase = 128 // W
+    log_cin = bz - lv
+    log_cout = bx - lv
+    assert log_cin >= 0 and log_cout >= 0
+    cin = 1 << log_cin
+    mask = min(cin, phase) - 1
+    chunks = 1 << (bx + log_cin)
+    smem = {}
+    for t, base in enumerate(srcs):
+        for q in range(chunks):
+            x, c = q >> log_cin, q & (cin - 1)
+            X = brev(x, bx) if rev else x
+            pc = c ^ ((X >> lv) & mask)
+            assert 0 <= pc < cin
+            s = t * chunks + (X << log_cin) + pc
+            assert s not in smem and 0 <= s < len(srcs) * chunks
+            els = []
+            for e in range(V):
+                g = base + x * stride_in + c * V + e
+                assert 0 <= g < n
+                loads.append(g)
+                els.append(g)
+            smem[s] = els
+    units = 1 << (log_cin + log_cout)
+    for t, dbase in enumerate(dsts):
+        for u in range(units):
+            c, d = u >> log_cout, u & ((1 << log_cout) - 1)
+            pc = c ^ (d & mask)
+            blk = [smem[t * chunks + ((d * V + j) << log_cin) + pc] for j in range(V)]
+            for e in range(V):
+                z = c * V + e
+                Z = brev(z, bz) if rev else z
+                for j in range(V):
+                    g = dbase + Z * stride_out + d * V + j
+                    assert 0 <= g < n
+                    stores.append((g, blk[j][e]))
+
+
+TARGET_B = {16: 5, 8: 5, 4: 6, 2: 7, 1: 8}
+
+
+def transpose_tiles(a, c, E, vec16=True):
+    """The host's tile choice for an out-of-place transposition."""
+    B = TARGET_B[E]
+    T = 2 * B
+    lv = (16 // E).bit_length() - 1
+    bz0 = min(c, B)
+    bx = min(a, T - bz0)
+    bz = min(c, T - bx)
+    W = 16 if (vec16 and bx >= lv and bz >= lv) else E
+    return bx, bz, W
+
+
+def check_perm(n, loads, stores, expected_src_of_dst):
+    assert sorted(loads) == list(range(n))
+    assert sorted(g for g, _ in stores) == list(range(n))
+    for g, s in stores:
+        assert s == expected_src_of_dst[g]
+
+
+def transpose_src_of_dst(a, c):
+    R, C = 1 << a, 1 << c
+    out = np.empty(R * C, dtype=np.int64)
+    for i in range(R):
+        for j in range(C):
+            out[j * R + i] = i * C + j
+    return out
+
+
+@pytest.mark.parametrize("E", (16, 8, 4, 2, 1))
+def test_transpose_oop_index_math(E):
+    for a, c in ((0, 0), (0, 5), (5, 0), (1, 9), (9, 1), (3, 4), (6, 6), (7, 2), (2, 11),
+                 (11, 3)):
+        for vec in (True, False):
+            bx, bz, W = transpose_tiles(a, c, E, vec)
+            n = 1 << (a + c)
+            loads, stores = [], []
+            for t in range(1 << ((a - bx) + (c - bz))):
+                tr, tc = t >> (c - bz), t & ((1 << (c - bz)) - 1)
+                emulate_g(E, W, 256, False, [(tr << (bx + c)) + (tc << bz)],
+                          [(tc << (bz + a)) + (tr << bx)], 1 << c, 1 << a, bx, bz, n,
+                          loads, stores)
+            check_perm(n, loads, stores, transpose_src_of_dst(a, c))
+
+
+def unrank_upper(q):
+    import math
+    col = int((1.0 + math.sqrt(1.0 + 8.0 * q)) * 0.5)
+    while col * (col - 1) // 2 > q:
+        col -= 1
+    while (col + 1) * col // 2 <= q:
+        col += 1
+    return q - col * (col - 1) // 2, col
+
+
+def test_upper_triangle_unranking():
+    for T in (1, 2, 3, 8, 33, 256):
+        got = [unrank_upper(q) for q in range(T * (T - 1) // 2)]
+        assert got == [(r, c) for c in range(T) for r in range(c)]
+    # large indices: consistency at the column boundaries
+    for col in (1 << 12, (1 << 14) - 1, 1 << 15):
+        q0 = col * (col - 1) // 2
+        assert unrank_upper(q0) == (0, col)
+        assert unrank_upper(q0 - 1) == (col - 2, col - 1)
+
+
+@pytest.mark.parametrize("E", (16, 8, 4, 1))
+def test_transpose_inplace_index_math(E):
+    lv = (16 // E).bit_length() - 1
+    for a in (0, 1, 2, 5, 7, 8):
+        b = min(a, TARGET_B[E])
+        W = 16 if b >= lv else E
+        Tn = 1 << (a - b)
+        n = 1 << (2 * a)
+        loads, stores = [], []
+        npairs = Tn * (Tn - 1) // 2
+        for q in range(npairs + Tn):
+            if q < npairs:
+                tr, tc = unrank_upper(q)
+                assert tr < tc < Tn
+                A = (tr << (b + a)) + (tc << b)
+                B_ = (tc << (b + a)) + (tr << b)
+                emulate_g(E, W, 256, False, [A, B_], [B_, A], 1 << a, 1 << a, b, b, n,
+                          loads, stores)
+            else:
+                tr = tc = q - npairs
+                A = (tr << (b + a)) + (tc << b)
+                emulate_g(E, W, 256, False, [A], [A], 1 << a, 1 << a, b, b, n, loads, stores)
+        if a:
+            check_perm(n, loads, stores, transpose_src_of_dst(a, a))
+
+
+def segment_choice(m, E):
+    b_min = {16: 3, 8: 4, 4: 5, 2: 6, 1: 7}[E]
+    if m < 2 * b_min:
+        return 0
+    return min(TARGET_B[E] - (1 if E <= 2 else 0), m // 2)
+
+
+@pytest.mark.parametrize("E", (16, 8, 4, 2))
+def test_segments_index_math(E):
+    for s_log, m in ((0, 12), (3, 10), (4, 13), (2, 15)):
+        b = segment_choice(m, E)
+        if b == 0:
+            continue
+        n = 1 << (s_log + m)
+        w = m - 2 * b
+        units = count_lt(w) + count_self(w)
+        loads, stores = [], []
+        for qq in range(units << s_log):
+            seg, q = qq // units, qq % units
+            base = seg << m
+            if q < count_lt(w):
+                y = unrank_lt(q, w)
+                ry = brev(y, w)
+                srcs, dsts = [base + (y << b), base + (ry << b)], [base + (ry << b),
+                                                                   base + (y << b)]
+            else:
+                y = unrank_self(q - count_lt(w), w)
+                srcs = dsts = [base + (y << b)]
+            emulate_g(E, 16, 256, True, srcs, dsts, 1 << (m - b), 1 << (m - b), b, b, n,
+                      loads, stores)
+        exp = np.array([((g >> m) << m) + brev(g & ((1 << m) - 1), m) for g in range(n)])
+        check_perm(n, loads, stores, exp)
+
+
+def test_recursive_composition_math():
+    """The three passes of the recursive ablation compose to the full
+    permutation (even k), and the odd-k route with its even-odd step too."""
+    def seg_rev(v, h):
+        s = 1 << h
+        return np.concatenate([v[r * s:(r + 1) * s][[brev(j, h) for j in range(s)]]
+                               for r in range(len(v) // s)])
+
+    def transpose_sq(v, h):
+        s = 1 << h
+        return v.reshape(s, s).T.reshape(-1)
+
+    for k in (2, 4, 6, 8, 10):
+        h = k // 2
+        v = np.arange(1 << k)
+        out = seg_rev(transpose_sq(seg_rev(v, h), h), h)
+        assert out.tolist() == [brev(j, k) for j in range(1 << k)]
+    for k in (3, 5, 7, 9):
+        v = np.arange(1 << k)
+        eo = np.concatenate([v[0::2], v[1::2]])
+        h = (k - 1) // 2
+        halves = [seg_rev(transpose_sq(seg_rev(part, h), h), h)
+                  for part in (eo[: 1 << (k - 1)], eo[1 << (k - 1):])]
+        assert np.concatenate(halves).tolist() == [brev(j, k) for j in range(1 << k)]
