@@ -39,7 +39,7 @@ def build(force: bool = False) -> str:
     if force or stale:
         tmp = LIB_PATH + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c99", "-D_POSIX_C_SOURCE=200809L", "-fPIC",
-               "-shared", "-pthread", "-Wall", "-Wextra", "-o", tmp, _SRC]
+               "-shared", "-pthread", "-Wall", "-Wextra", "-o", tmp, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, LIB_PATH)
     return LIB_PATH
@@ -69,6 +69,8 @@ def lib() -> ctypes.CDLL:
             L.oracle_even_odd.restype = i32
             L.oracle_perfect_shuffle.argtypes = [vp, vp, i32, i32]
             L.oracle_perfect_shuffle.restype = i32
+            L.oracle_fft_dit_stages.argtypes = [vp, vp, i32, i32, i32]
+            L.oracle_fft_dit_stages.restype = i32
             _lib = L
     return _lib
 
@@ -157,3 +159,15 @@ def perfect_shuffle(src: np.ndarray, k: int, elem_bytes: int) -> np.ndarray:
     if lib().oracle_perfect_shuffle(d.ctypes.data, s.ctypes.data, k, elem_bytes) != 0:
         raise ValueError("oracle_perfect_shuffle rejected its arguments")
     return d
+
+
+def fft_dit_stages(x: np.ndarray, k: int, stages: int, inverse: bool = False) -> np.ndarray:
+    """First `stages` radix-2 DIT stages of the bit-reversed ``x`` (complex,
+    2^k values); computed in double, returned as complex128."""
+    z = np.ascontiguousarray(np.asarray(x, dtype=np.complex128).reshape(-1))
+    assert z.size == 1 << k
+    out = np.empty_like(z)
+    if lib().oracle_fft_dit_stages(out.ctypes.data, z.ctypes.data, k, stages,
+                                   int(bool(inverse))) != 0:
+        raise ValueError("oracle_fft_dit_stages rejected its arguments")
+    return out

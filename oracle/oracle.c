@@ -9,6 +9,7 @@
  */
 #include "oracle.h"
 
+#include <math.h>
 #include <pthread.h>
 #include <stdlib.h>
 #include <string.h>
@@ -221,6 +222,40 @@ int oracle_perfect_shuffle(void *dst, const void *src, int k, int elem_bytes)
                (size_t)elem_bytes);
         memcpy(d + (2 * i + 1) * (uint64_t)elem_bytes, s + (h + i) * (uint64_t)elem_bytes,
                (size_t)elem_bytes);
+    }
+    return 0;
+}
+
+/* Bit-reversed permutation, then the textbook radix-2 DIT butterflies stage
+ * by stage, twiddles from cos/sin of the exact angle. */
+int oracle_fft_dit_stages(double *out, const double *in, int k, int stages, int inverse)
+{
+    uint64_t n, m, h, base, j;
+    int s;
+    const double two_pi = 6.283185307179586476925286766559;
+    if (k < 0 || k > 30 || stages < 0 || stages > k || !out || !in)
+        return -1;
+    if (oracle_brev_oop(out, in, k, 2 * (int)sizeof(double)) != 0)
+        return -1;
+    n = (uint64_t)1 << k;
+    for (s = 1; s <= stages; ++s) {
+        m = (uint64_t)1 << s;
+        h = m / 2;
+        for (base = 0; base < n; base += m) {
+            for (j = 0; j < h; ++j) {
+                const double ang = two_pi * (double)j / (double)m;
+                const double wr = cos(ang), wi = inverse ? sin(ang) : -sin(ang);
+                double *a = out + 2 * (base + j);
+                double *b = out + 2 * (base + j + h);
+                const double tr = b[0] * wr - b[1] * wi;
+                const double ti = b[0] * wi + b[1] * wr;
+                const double ar = a[0], ai = a[1];
+                a[0] = ar + tr;
+                a[1] = ai + ti;
+                b[0] = ar - tr;
+                b[1] = ai - ti;
+            }
+        }
     }
     return 0;
 }

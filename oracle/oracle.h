@@ -65,6 +65,18 @@ int oracle_even_odd(void *dst, const void *src, int k, int elem_bytes);
  * Returns 0 or -1. */
 int oracle_perfect_shuffle(void *dst, const void *src, int k, int elem_bytes);
 
+/* The first `stages` stages of the iterative radix-2 decimation-in-time FFT
+ * applied after the bit-reversed permutation (Introduction: once the
+ * permutation has been applied, every level of the Cooley-Tukey recursion
+ * finds its even-odd split already done).  in and out hold n = 2^k complex
+ * numbers as interleaved (re, im) doubles; out = stages of rev-permuted in,
+ * all arithmetic in double.  Stage s (1-based) combines, in every block of
+ * m = 2^s consecutive elements, a[j] and a[j + m/2] (j < m/2) with the twiddle
+ * w = exp(-2 pi i j / m) (exp(+...) when inverse != 0):
+ *   (a[j], a[j + m/2]) <- (a[j] + w a[j + m/2], a[j] - w a[j + m/2]).
+ * stages = k gives the full (unnormalised) DFT.  Returns 0 or -1. */
+int oracle_fft_dit_stages(double *out, const double *in, int k, int stages, int inverse);
+
 #ifdef __cplusplus
 }
 #endif

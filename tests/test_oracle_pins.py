@@ -277,3 +277,58 @@ def test_recursive_method_with_c_transpose(oracle_lib):
             t = oracle_lib.transpose(np.concatenate(blocks), h, h, E)
             blocks = [oracle_lib.brev_oop(t[r * s * E:(r + 1) * s * E], h, E) for r in range(s)]
             assert np.array_equal(np.concatenate(blocks), oracle_lib.brev_oop(x, k, E))
+
+
+# ------------------------------------------- bit reversal + FFT stages --
+def test_fft_stages_full_equals_numpy_dft(oracle_lib):
+    """stages = k is the whole FFT: numpy's FFT (a library routine) and, for
+    small n, the DFT sum written out."""
+    rng = np.random.default_rng(1)
+    for k in range(0, 13):
+        x = rng.uniform(-1, 1, 1 << k) + 1j * rng.uniform(-1, 1, 1 << k)
+        got = oracle_lib.fft_dit_stages(x, k, k)
+        exp = np.fft.fft(x)
+        assert np.max(np.abs(got - exp)) <= 1e-12 * max(1, np.max(np.abs(exp))) * (k + 1)
+        inv = oracle_lib.fft_dit_stages(x, k, k, inverse=True)
+        assert np.max(np.abs(inv - np.fft.ifft(x) * (1 << k))) <= 1e-12 * (1 << k) * (k + 1)
+    for k in (2, 3, 5):
+        n = 1 << k
+        x = rng.uniform(-1, 1, n) + 1j * rng.uniform(-1, 1, n)
+        dft = np.array([sum(x[t] * np.exp(-2j * np.pi * f * t / n) for t in range(n))
+                        for f in range(n)])
+        assert np.allclose(oracle_lib.fft_dit_stages(x, k, k), dft, atol=1e-12)
+
+
+def test_fft_stages_partial_structure(oracle_lib):
+    """stages = 0 is the permutation; after s stages every block of 2^s
+    consecutive outputs is the 2^s-point DFT of its (bit-reversed) inputs,
+    i.e. the DFT of the inputs spaced n / 2^s apart."""
+    rng = np.random.default_rng(2)
+    for k in (4, 7, 10):
+        n = 1 << k
+        x = rng.uniform(-1, 1, n) + 1j * rng.uniform(-1, 1, n)
+        perm = oracle_lib.brev_oop(x.astype(np.complex128), k, 16).view(np.complex128)
+        assert np.array_equal(oracle_lib.fft_dit_stages(x, k, 0), perm)
+        for s in range(1, k + 1):
+            got = oracle_lib.fft_dit_stages(x, k, s)
+            m = 1 << s
+            for blk in range(0, n // m, max(1, (n // m) // 4)):
+                # block `blk` holds inputs with index = rev_{k-s}(blk) + t * (n / m)
+                r = oracle_lib.rev_bits(blk, k - s)
+                sub = x[r::n // m]
+                assert np.allclose(got[blk * m:(blk + 1) * m], np.fft.fft(sub), atol=1e-11)
+
+
+def test_fft_stages_impulse_and_linearity(oracle_lib):
+    k = 9
+    n = 1 << k
+    d = np.zeros(n, dtype=np.complex128)
+    d[0] = 1
+    assert np.allclose(oracle_lib.fft_dit_stages(d, k, k), np.ones(n))
+    rng = np.random.default_rng(3)
+    a = rng.normal(size=n) + 1j * rng.normal(size=n)
+    b = rng.normal(size=n) + 1j * rng.normal(size=n)
+    for s in (1, 4, k):
+        lhs = oracle_lib.fft_dit_stages(2 * a - 3j * b, k, s)
+        rhs = 2 * oracle_lib.fft_dit_stages(a, k, s) - 3j * oracle_lib.fft_dit_stages(b, k, s)
+        assert np.allclose(lhs, rhs, atol=1e-10)
