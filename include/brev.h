@@ -182,6 +182,26 @@ BREV_API brev_status brev_permute_segments(void *data, int log2_segments, int lo
 BREV_API brev_status brev_permute_recursive(void *data, int log2n, int elem_bytes,
                                             void *stream);
 
+/* ---------------------------------------------------------------- fused FFT stages */
+
+/* The bit-reversed permutation fused with the first `stages` radix-2
+ * decimation-in-time FFT stages (Introduction: after the permutation, every
+ * level of the Cooley-Tukey recursion finds its even-odd split already
+ * done).  dst = stages 1..S applied to the permuted src, where stage s
+ * combines, in each block of m = 2^s consecutive elements, a[j] and
+ * a[j + m/2] (j < m/2) with w = exp(-2 pi i j / m) (the conjugate when
+ * inverse != 0): (a[j], a[j+m/2]) <- (a[j] + w a[j+m/2], a[j] - w a[j+m/2]).
+ * elem_bytes 8 = complex<float> (float arithmetic) or 16 = complex<double>
+ * (double arithmetic); arrays 16-byte aligned; dst == src runs in place.
+ * The butterflies run on the shared-memory tile between load and store, so
+ * permutation and stages take one HBM round trip.  stages = 0 is the plain
+ * permutation; stages up to 6 are supported for every size (up to log2n
+ * when the whole array fits one CTA); more return BREV_ERR_UNSUPPORTED.
+ * Results are floating point: they match a double-precision reference to
+ * within rounding (see the tests for the bound). */
+BREV_API brev_status brev_fft_stages(void *dst, const void *src, int log2n, int elem_bytes,
+                                     int stages, int inverse, void *stream);
+
 /* ---------------------------------------------------------------- host path */
 
 /* End-to-end form for host buffers: permutes src_host (2^log2n elements)

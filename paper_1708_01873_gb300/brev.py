@@ -51,6 +51,7 @@ SIGNATURES = {
     "brev_perfect_shuffle": (_i, [_vp, _vp, _i, _i, _vp]),
     "brev_permute_segments": (_i, [_vp, _i, _i, _i, _vp]),
     "brev_permute_recursive": (_i, [_vp, _i, _i, _vp]),
+    "brev_fft_stages": (_i, [_vp, _vp, _i, _i, _i, _i, _vp]),
     "brev_tile_shape": (_i, [_i, _i, _i, _ip, _ip, _ip]),
     "brev_permute_shape": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _vp]),
     "brev_shape_count": (_i, [_i, _i]),
@@ -287,6 +288,17 @@ def brev_permute_recursive(data, stream=None) -> None:
     _check(lib().brev_permute_recursive(data.data_ptr(), _log2(data.numel()),
                                         data.element_size(), _stream_handle(stream, data.device)),
            "brev_permute_recursive")
+
+
+def brev_fft_stages(dst, src, stages: int, inverse: bool = False, stream=None) -> None:
+    """dst = first `stages` radix-2 DIT FFT stages of the bit-reversed src
+    (complex64 or complex128 tensors; dst may be src)."""
+    _flat(dst), _flat(src)
+    if dst.numel() != src.numel() or dst.element_size() != src.element_size():
+        raise ValueError("dst and src must match")
+    _check(lib().brev_fft_stages(dst.data_ptr(), src.data_ptr(), _log2(src.numel()),
+                                 src.element_size(), stages, int(bool(inverse)),
+                                 _stream_handle(stream, src.device)), "brev_fft_stages")
 
 
 # -------------------------------------------------------------- host --

@@ -1,0 +1,273 @@
+// Bit-reversed permutation fused with the first S radix-2 decimation-in-time
+// FFT stages, for complex<float> (E = 8, float arithmetic) and
+// complex<double> (E = 16, double arithmetic).
+//
+// The paper's motivation (Introduction): once the bit-reversed permutation
+// has been applied, each level of the Cooley-Tukey recursion finds its
+// even-odd split done, so the FFT proper is a sequence of butterfly stages
+// over contiguous blocks.  Stage s combines, in every block of m = 2^s
+// consecutive elements, a[j] and a[j + m/2] with w = exp(-2 pi i j / m).
+// The tile kernel's output rows are contiguous runs of 2^B elements aligned
+// to 2^B, so the first S <= B stages act inside one output row: after the
+// tile is staged and transposed in shared memory (output row rev(z) is
+// shared-memory column z), the butterflies run there and the tile is stored
+// once -- the permutation and S stages in a single HBM round trip instead of
+// one pass for the permutation and another for the stages.
+#include <algorithm>
+
+#include "brev_device.cuh"
+#include "brev_internal.h"
+
+namespace brev {
+
+template <int E> struct Cplx;
+template <> struct Cplx<8> { using T = float2; using R = float; };
+template <> struct Cplx<16> { using T = double2; using R = double; };
+
+// Element (X, z) of a staged tile (row X = rev(x), column z).
+template <class G>
+__device__ __forceinline__ typename Cplx<G::E>::T* tile_elem(uint4* sm, int X, int z) {
+  constexpr int LOG_V = ilog2c(G::V);
+  const int chunk = X * G::CIN + ((z >> LOG_V) ^ ((X >> LOG_V) & G::SWZ));
+  return reinterpret_cast<typename Cplx<G::E>::T*>(sm + chunk) + (z & (G::V - 1));
+}
+
+// Twiddles w_{2^B}^i = exp(-2 pi i i / 2^B), i < 2^(B-1), into shared memory.
+template <int E, int B>
+__device__ __forceinline__ void fill_twiddles(typename Cplx<E>::T* tw) {
+  using R = typename Cplx<E>::R;
+  for (int i = threadIdx.x; i < (1 << (B - 1)); i += blockDim.x) {
+    double sn, cs;
+    sincospi((double)i / (double)(1 << (B - 1)), &sn, &cs);
+    tw[i].x = (R)cs;
+    tw[i].y = (R)(-sn);
+  }
+}
+
+// Stages 1..S on every output row of a staged tile (columns of sm).
+template <class G, int NTHR>
+__device__ __forceinline__ void dit_stages(uint4* sm, int S, int inverse,
+                                           const typename Cplx<G::E>::T* tw) {
+  using T = typename Cplx<G::E>::T;
+  constexpr int NB = 1 << (G::BX + G::BZ - 1);  // butterflies per stage
+  for (int s = 1; s <= S; ++s) {
+    const int h = 1 << (s - 1);
+#pragma unroll 2
+    for (int u = threadIdx.x; u < NB; u += NTHR) {
+      const int z = u & ((1 << G::BZ) - 1);
+      const int p = u >> G::BZ;
+      const int j = p & (h - 1);
+      const int X0 = ((p >> (s - 1)) << s) + j;
+      T* pa = tile_elem<G>(sm, X0, z);
+      T* pb = tile_elem<G>(sm, X0 + h, z);
+      T w = tw[j << (G::BX - s)];
+      if (inverse) w.y = -w.y;
+      const T a = *pa, b = *pb;
+      T t;
+      t.x = b.x * w.x - b.y * w.y;
+      t.y = b.x * w.y + b.y * w.x;
+      T o0, o1;
+      o0.x = a.x + t.x;
+      o0.y = a.y + t.y;
+      o1.x = a.x - t.x;
+      o1.y = a.y - t.y;
+      *pa = o0;
+      *pb = o1;
+    }
+    __syncthreads();
+  }
+}
+
+template <int E, int B>
+__global__ void __launch_bounds__(Geom<E, 16, B, B>::THREADS)
+    k_fft_oop(char* __restrict__ dst, const char* __restrict__ src, int k, int S,
+              int inverse) {
+  using G = Geom<E, 16, B, B>;
+  using T = typename Cplx<E>::T;
+  extern __shared__ uint4 smem_u4[];
+  T* tw = reinterpret_cast<T*>(smem_u4 + G::CHUNKS);
+  fill_twiddles<E, B>(tw);
+  const int wy = k - 2 * B;
+  const uint32_t y = blockIdx.x;
+  const uint32_t ry = rev_bits(y, wy);
+  const uint64_t stride = (uint64_t)E << (k - B);
+  load_tiles<G, true, G::THREADS, 1>(smem_u4, src + ((uint64_t)y << B) * E, nullptr, stride, 1);
+  __syncthreads();
+  dit_stages<G, G::THREADS>(smem_u4, S, inverse, tw);
+  store_tile<G, G::THREADS>(smem_u4, dst + ((uint64_t)ry << B) * E, stride);
+}
+
+template <int E, int B>
+__global__ void __launch_bounds__(Geom<E, 16, B, B>::THREADS)
+    k_fft_inplace(char* data, int k, int S, int inverse) {
+  using G = Geom<E, 16, B, B>;
+  using T = typename Cplx<E>::T;
+  extern __shared__ uint4 smem_u4[];
+  T* tw = reinterpret_cast<T*>(smem_u4 + 2 * G::CHUNKS);
+  fill_twiddles<E, B>(tw);
+  const int wy = k - 2 * B;
+  const uint32_t npairs = count_lt(wy);
+  const uint32_t q = blockIdx.x;
+  uint32_t y, ry;
+  int nt;
+  if (q < npairs) {
+    y = unrank_lt(q, wy);
+    ry = rev_bits(y, wy);
+    nt = 2;
+  } else {
+    y = unrank_self(q - npairs, wy);
+    ry = y;
+    nt = 1;
+  }
+  const uint64_t stride = (uint64_t)E << (k - B);
+  char* const ty = data + ((uint64_t)y << B) * E;
+  char* const tr = data + ((uint64_t)ry << B) * E;
+  load_tiles<G, false, G::THREADS, 2>(smem_u4, ty, tr, stride, nt);
+  __syncthreads();
+  dit_stages<G, G::THREADS>(smem_u4, S, inverse, tw);
+  if (nt == 2) dit_stages<G, G::THREADS>(smem_u4 + G::CHUNKS, S, inverse, tw);
+  store_tile<G, G::THREADS>(smem_u4, tr, stride);
+  if (nt == 2) store_tile<G, G::THREADS>(smem_u4 + G::CHUNKS, ty, stride);
+}
+
+// Small arrays (and any array that fits): one CTA stages the permuted array
+// in shared memory, runs the stages, and stores it.
+template <int E>
+__global__ void __launch_bounds__(256) k_fft_small(char* dst, const char* src, int k, int S,
+                                                 int inverse) {
+  using T = typename Cplx<E>::T;
+  extern __shared__ uint4 smem_u4[];
+  T* a = reinterpret_cast<T*>(smem_u4);
+  const uint32_t n = 1u << k;
+  const T* s = reinterpret_cast<const T*>(src);
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) a[rev_bits(i, k)] = s[i];
+  __syncthreads();
+  for (int st = 1; st <= S; ++st) {
+    const uint32_t h = 1u << (st - 1);
+    for (uint32_t p = threadIdx.x; p < n / 2; p += blockDim.x) {
+      const uint32_t j = p & (h - 1);
+      const uint32_t i0 = ((p >> (st - 1)) << st) + j;
+      double sn, cs;
+      sincospi((double)j / (double)h, &sn, &cs);
+      T w;
+      w.x = (typename Cplx<E>::R)cs;
+      w.y = (typename Cplx<E>::R)(inverse ? sn : -sn);
+      const T x0 = a[i0], x1 = a[i0 + h];
+      T t;
+      t.x = x1.x * w.x - x1.y * w.y;
+      t.y = x1.x * w.y + x1.y * w.x;
+      a[i0].x = x0.x + t.x;
+      a[i0].y = x0.y + t.y;
+      a[i0 + h].x = x0.x - t.x;
+      a[i0 + h].y = x0.y - t.y;
+    }
+    __syncthreads();
+  }
+  T* d = reinterpret_cast<T*>(dst);
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) d[i] = a[i];
+}
+
+// ------------------------------------------------------------------ host --
+
+struct FftKernel {
+  const void* oop;
+  const void* inplace;
+  int B, threads;
+  unsigned tile_bytes;
+};
+
+template <int E, int B>
+static FftKernel fft_k() {
+  using G = Geom<E, 16, B, B>;
+  return {(const void*)&k_fft_oop<E, B>, (const void*)&k_fft_inplace<E, B>, B, G::THREADS,
+          G::TILE_BYTES};
+}
+
+static bool fft_lookup(int E, int B, FftKernel* out) {
+  switch (E * 16 + B) {
+    case 16 * 16 + 3: *out = fft_k<16, 3>(); return true;
+    case 16 * 16 + 4: *out = fft_k<16, 4>(); return true;
+    case 16 * 16 + 5: *out = fft_k<16, 5>(); return true;
+    case 16 * 16 + 6: *out = fft_k<16, 6>(); return true;
+    case 8 * 16 + 4: *out = fft_k<8, 4>(); return true;
+    case 8 * 16 + 5: *out = fft_k<8, 5>(); return true;
+    case 8 * 16 + 6: *out = fft_k<8, 6>(); return true;
+  }
+  return false;
+}
+
+}  // namespace brev
+
+using namespace brev;
+
+extern "C" brev_status brev_fft_stages(void* dst, const void* src, int log2n, int elem_bytes,
+                                       int stages, int inverse, void* stream) {
+  const int E = elem_bytes, k = log2n, S = stages;
+  if (E != 8 && E != 16)
+    return set_error(BREV_ERR_INVALID_ARG, "elem_bytes=%d (complex<float> 8 or complex<double> 16)",
+                     E);
+  if (k < 0 || k > 31) return set_error(BREV_ERR_INVALID_ARG, "log2n=%d", k);
+  if (S < 0 || S > k) return set_error(BREV_ERR_INVALID_ARG, "stages=%d for log2n=%d", S, k);
+  if (!dst || !src) return set_error(BREV_ERR_INVALID_ARG, "NULL data pointer");
+  if ((uintptr_t)dst % 16 || (uintptr_t)src % 16)
+    return set_error(BREV_ERR_ALIGNMENT, "complex arrays must be 16-byte aligned");
+  const uint64_t bytes = (uint64_t)E << k;
+  if (dst != src) {
+    const uint64_t d = (uintptr_t)dst, s = (uintptr_t)src;
+    if (d < s + bytes && s < d + bytes)
+      return set_error(BREV_ERR_OVERLAP, "source and destination overlap partially");
+  }
+  brev_status st = check_device_range(src, bytes, "source");
+  if (st == BREV_OK && dst != src) st = check_device_range(dst, bytes, "destination");
+  if (st != BREV_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool inplace = dst == src;
+  const int pref = E == 16 ? 5 : 6;
+  int B = std::max(S, std::min(pref, k / 2));
+  FftKernel K{};
+  const bool tiles = 2 * B <= k && B >= b_min_for(E) && fft_lookup(E, B, &K);
+  cudaError_t e;
+  if (!tiles) {
+    // whole array in one CTA when it fits in shared memory
+    const unsigned smem = (unsigned)E << k;
+    if (smem > 96 * 1024)
+      return set_error(BREV_ERR_UNSUPPORTED,
+                       "%d stages need tile rows of 2^%d elements, not compiled for k=%d E=%d", S,
+                       B, k, E);
+    const void* kern = E == 16 ? (const void*)&k_fft_small<16> : (const void*)&k_fft_small<8>;
+    e = ensure_smem(kern, smem);
+    if (e != cudaSuccess) return cuda_error(e, "shared-memory limit");
+    char* d = (char*)dst;
+    const char* sr = (const char*)src;
+    int kk = k, SS = S, inv = inverse ? 1 : 0;
+    void* args[] = {(void*)&d, (void*)&sr, (void*)&kk, (void*)&SS, (void*)&inv};
+    e = cudaLaunchKernel(kern, dim3(1), dim3(256), args, smem, s);
+    if (e != cudaSuccess) return cuda_error(e, "fused FFT launch");
+    note_launch();
+    return BREV_OK;
+  }
+  const unsigned tw_bytes = (unsigned)E << (K.B - 1);
+  int kk = k, SS = S, inv = inverse ? 1 : 0;
+  if (inplace) {
+    const int w = k - 2 * K.B;
+    const unsigned long long grid = (unsigned long long)count_lt(w) + count_self(w);
+    const unsigned smem = 2 * K.tile_bytes + tw_bytes;
+    e = ensure_smem(K.inplace, smem);
+    if (e != cudaSuccess) return cuda_error(e, "shared-memory limit");
+    char* d = (char*)dst;
+    void* args[] = {(void*)&d, (void*)&kk, (void*)&SS, (void*)&inv};
+    e = cudaLaunchKernel(K.inplace, dim3((unsigned)grid), dim3(K.threads), args, smem, s);
+  } else {
+    const unsigned long long grid = 1ull << (k - 2 * K.B);
+    const unsigned smem = K.tile_bytes + tw_bytes;
+    e = ensure_smem(K.oop, smem);
+    if (e != cudaSuccess) return cuda_error(e, "shared-memory limit");
+    char* d = (char*)dst;
+    const char* sr = (const char*)src;
+    void* args[] = {(void*)&d, (void*)&sr, (void*)&kk, (void*)&SS, (void*)&inv};
+    e = cudaLaunchKernel(K.oop, dim3((unsigned)grid), dim3(K.threads), args, smem, s);
+  }
+  if (e != cudaSuccess) return cuda_error(e, "fused FFT launch");
+  note_launch();
+  return BREV_OK;
+}

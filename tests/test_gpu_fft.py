@@ -1,0 +1,113 @@
+"""Bit reversal fused with the first radix-2 DIT FFT stages, GPU vs the CPU
+oracle (double precision).
+
+Tolerance (derived from the arithmetic): inputs lie in [-1, 1) per
+component.  After s stages every value is a sum of 2^s inputs times unit
+twiddles, so |value| <= 2^s * sqrt(2).  Each stage rounds a complex product
+(about 3 ulp) and a sum (1 ulp), so the error grows by at most
+4 eps * 2^s * sqrt(2) per stage, and after S stages the absolute error
+per component is below (S + 1) * 8 * eps * 2^S, with eps = 2^-24 for
+complex<float> (float arithmetic; the oracle is exact to 2^-53 by
+comparison) and 2^-53 for complex<double>.  Zero stages are the plain
+permutation and must match bit for bit.
+"""
+import numpy as np
+import pytest
+import torch
+
+from gpu_util import DTYPE, KIND, device_array, host_array, to_bytes
+from paper_1708_01873_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+EPS = {8: 2.0 ** -24, 16: 2.0 ** -53}
+
+
+def tol(E, S):
+    return (S + 1) * 8 * EPS[E] * 2.0 ** S
+
+
+def as_complex(b: np.ndarray, E: int) -> np.ndarray:
+    return b.view(np.complex64 if E == 8 else np.complex128).astype(np.complex128)
+
+
+def check(got_bytes, x, k, E, S, inverse, what):
+    exp = __import__("oracle").fft_dit_stages(x, k, S, inverse)
+    got = as_complex(got_bytes, E)
+    if S == 0:
+        assert np.array_equal(got, exp), what
+        return
+    err = np.max(np.abs(got - exp)) if got.size else 0.0
+    assert err <= tol(E, S), f"{what}: max error {err:.3e} > {tol(E, S):.3e}"
+
+
+@pytest.mark.parametrize("E", (8, 16))
+def test_fused_stages_vs_oracle(brev_lib, oracle_lib, cuda_device, E):
+    for k in list(range(0, 15)) + [17, 20]:
+        for S in sorted({0, 1, 3, min(k, 5), min(k, 6)}):
+            if S > k:
+                continue
+            for inplace in (False, True):
+                for inverse in (False, True):
+                    seed = 1000 * k + 10 * S + E + 2 * inverse + inplace
+                    src = device_array(seed, k, E)
+                    x = as_complex(host_array(seed, k, E), E)
+                    if inplace:
+                        brev_lib.brev_fft_stages(src, src, S, inverse)
+                        out = src
+                    else:
+                        out = torch.empty_like(src)
+                        brev_lib.brev_fft_stages(out, src, S, inverse)
+                    check(to_bytes(out), x, k, E, S, inverse,
+                          f"k={k} S={S} E={E} inplace={inplace} inverse={inverse}")
+
+
+@pytest.mark.parametrize("E", (8, 16))
+def test_full_fft_small_arrays(brev_lib, oracle_lib, cuda_device, E):
+    """All stages in one CTA for arrays that fit: the whole FFT."""
+    for k in range(1, 12):
+        seed = 5000 + k + E
+        src = device_array(seed, k, E)
+        x = as_complex(host_array(seed, k, E), E)
+        out = torch.empty_like(src)
+        brev_lib.brev_fft_stages(out, src, k)
+        check(to_bytes(out), x, k, E, k, False, f"full FFT k={k}")
+        assert np.allclose(as_complex(to_bytes(out), E), np.fft.fft(x),
+                           atol=tol(E, k) * 4)
+
+
+@pytest.mark.parametrize("k,E,S", [(26, 8, 6), (26, 16, 5), (27, 8, 5)])
+def test_fused_full_size_sampled_blocks(brev_lib, oracle_lib, cuda_device, k, E, S):
+    """After S stages, output block b (2^S elements) is the S-stage result of
+    the inputs spaced n / 2^S apart starting at rev_{k-S}(b) (pinned on the
+    oracle); sampled blocks are checked against the oracle on those inputs,
+    regenerated from the seed."""
+    seed = 7000 + k
+    src = device_array(seed, k, E)
+    out = torch.empty_like(src)
+    brev_lib.brev_fft_stages(out, src, S)
+    torch.cuda.synchronize()
+    n, m = 1 << k, 1 << S
+    rng = np.random.default_rng(k)
+    blocks = np.concatenate([rng.integers(0, n // m, size=64), [0, n // m - 1]])
+    got = out.view(torch.uint8).view(-1, m * E)
+    for b in blocks.tolist():
+        r = oracle_lib.rev_bits(b, k - S)
+        idx = np.arange(r, n, n // m, dtype=np.uint64)
+        sub = as_complex(inputs.elements_np(seed, idx, KIND[E]).reshape(-1), E)
+        exp = oracle_lib.fft_dit_stages(sub, S, S)
+        g = as_complex(got[b].cpu().numpy(), E)
+        err = np.max(np.abs(g - exp))
+        assert err <= tol(E, S), f"block {b}: {err:.3e}"
+
+
+def test_fused_errors(brev_lib, cuda_device):
+    L = brev_lib.lib()
+    t = device_array(1, 20, 16)
+    p = t.data_ptr()
+    c0 = brev_lib.brev_launch_count()
+    assert L.brev_fft_stages(p, p, 20, 4, 3, 0, None) == 1      # not a complex size
+    assert L.brev_fft_stages(p, p, 20, 16, 21, 0, None) == 1    # more stages than bits
+    assert L.brev_fft_stages(p, p, 20, 16, 9, 0, None) == 6     # too many for a tile row
+    assert L.brev_fft_stages(p + 8, p + 8, 10, 16, 2, 0, None) == 2
+    assert brev_lib.brev_launch_count() == c0

@@ -544,3 +544,41 @@ def test_recursive_composition_math():
         halves = [seg_rev(transpose_sq(seg_rev(part, h), h), h)
                   for part in (eo[: 1 << (k - 1)], eo[1 << (k - 1):])]
         assert np.concatenate(halves).tolist() == [brev(j, k) for j in range(1 << k)]
+
+
+def test_fused_fft_butterfly_indexing():
+    """dit_stages' thread -> (column z, pair X0, twiddle index) mapping applies
+    every stage to every output row (a shared-memory column) exactly as the
+    textbook stage, with table index j * 2^(B-s) < 2^(B-1)."""
+    rng = np.random.default_rng(0)
+    for B in (3, 4, 5, 6):
+        BZ = B
+        table = np.exp(-2j * np.pi * np.arange(1 << (B - 1)) / (1 << B))
+        for S in range(0, B + 1):
+            cols = rng.normal(size=(1 << BZ, 1 << B)) + 1j * rng.normal(size=(1 << BZ, 1 << B))
+            got = cols.copy()
+            NB = 1 << (B + BZ - 1)
+            for s in range(1, S + 1):
+                h = 1 << (s - 1)
+                touched = set()
+                for u in range(NB):
+                    z = u & ((1 << BZ) - 1)
+                    p = u >> BZ
+                    j = p & (h - 1)
+                    X0 = ((p >> (s - 1)) << s) + j
+                    ti = j << (B - s)
+                    assert 0 <= X0 < X0 + h < (1 << B) and 0 <= ti < (1 << (B - 1))
+                    assert (z, X0) not in touched and (z, X0 + h) not in touched
+                    touched |= {(z, X0), (z, X0 + h)}
+                    a, b = got[z, X0], got[z, X0 + h] * table[ti]
+                    got[z, X0], got[z, X0 + h] = a + b, a - b
+                assert len(touched) == (1 << BZ) << B
+            exp = cols.copy()
+            for s in range(1, S + 1):
+                m, h = 1 << s, 1 << (s - 1)
+                for base in range(0, 1 << B, m):
+                    for j in range(h):
+                        w = np.exp(-2j * np.pi * j / m)
+                        a, b = exp[:, base + j].copy(), exp[:, base + j + h] * w
+                        exp[:, base + j], exp[:, base + j + h] = a + b, a - b
+            assert np.allclose(got, exp, atol=1e-12)
