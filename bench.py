@@ -451,6 +451,25 @@ def bench_next(torch, brev, inputs, device, stream, sampler, reduce_max, barrier
         "ratio": round(rec / one, 3),
         "one_pass_gbs": round(nbytes / (one * 1e-3) / 1e9, 1),
         "recursive_hbm_passes": 3}
+    # bit reversal fused with the first DIT FFT stages vs the plain permutation
+    for kind, E, S in (("c64", 8, 6), ("c128", 16, 5)):
+        k2 = 28
+        x = torch.empty((1 << k2) * E, dtype=torch.uint8, device=device)
+        inputs.fill_torch(x, 29, kind, chunk=1 << 26)
+        y = torch.empty_like(x)
+        nb = 2 * x.numel()
+        plain = timed(lambda: L.brev_permute_to(y.data_ptr(), x.data_ptr(), k2, E, sh))
+        fused = timed(lambda: L.brev_fft_stages(y.data_ptr(), x.data_ptr(), k2, E, S, 0, sh))
+        fused_ip = timed(lambda: L.brev_fft_stages(y.data_ptr(), y.data_ptr(), k2, E, S, 0, sh))
+        flops = 5.0 * (1 << k2) * S  # radix-2 butterfly stage: 5 n flops
+        out[f"fft_stages_{kind}_k28_S{S}"] = {
+            "permute_ms": round(plain, 4), "fused_ms": round(fused, 4),
+            "fused_in_place_ms": round(fused_ip, 4),
+            "fused_gbs": round(nb / (fused * 1e-3) / 1e9, 1),
+            "fused_frac": round(nb / (fused * 1e-3) / 1e9 / peak, 4),
+            "fused_gflops": round(flops / (fused * 1e-3) / 1e9, 1),
+            "stages_cost_vs_permute": round(fused / plain, 3)}
+        del x, y
     del src, dst
     return out
 

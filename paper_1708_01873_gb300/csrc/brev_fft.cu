@@ -44,36 +44,144 @@ __device__ __forceinline__ void fill_twiddles(typename Cplx<E>::T* tw) {
   }
 }
 
-// Stages 1..S on every output row of a staged tile (columns of sm).
+template <class T>
+__device__ __forceinline__ void butterfly(T& a, T& b, T w) {
+  T t;
+  t.x = b.x * w.x - b.y * w.y;
+  t.y = b.x * w.y + b.y * w.x;
+  b.x = a.x - t.x;
+  b.y = a.y - t.y;
+  a.x = a.x + t.x;
+  a.y = a.y + t.y;
+}
+
+// a * w for w = exp(-+2 pi i jj / 2^s) when jj is known at compile time:
+// w = 1 and w = -i (+i inverse) need no multiplication.
+template <class T, int S, int JJ>
+__device__ __forceinline__ T twiddle_const(T b, int inverse, const T* tw, int shift) {
+  if constexpr (JJ == 0) {
+    return b;
+  } else if constexpr (2 * JJ == (1 << (S - 1))) {  // a quarter turn
+    T t;
+    if (inverse) {  // +i b
+      t.x = -b.y;
+      t.y = b.x;
+    } else {  // -i b
+      t.x = b.y;
+      t.y = -b.x;
+    }
+    return t;
+  } else {
+    T w = tw[JJ << shift];
+    if (inverse) w.y = -w.y;
+    T t;
+    t.x = b.x * w.x - b.y * w.y;
+    t.y = b.x * w.y + b.y * w.x;
+    return t;
+  }
+}
+
+// Stages 1..R (R <= 3) of every output row, in registers, with the
+// twiddles resolved at compile time (groups are 2^R consecutive elements).
+template <class G, int NTHR, int R>
+__device__ __forceinline__ void dit_first_pass(uint4* sm, int inverse,
+                                               const typename Cplx<G::E>::T* tw) {
+  using T = typename Cplx<G::E>::T;
+  constexpr int GN = 1 << R;
+  const int groups = 1 << (G::BX + G::BZ - R);
+  for (int g = threadIdx.x; g < groups; g += NTHR) {
+    const int z = g & ((1 << G::BZ) - 1);
+    const int base = (g >> G::BZ) << R;
+    T v[GN];
+#pragma unroll
+    for (int t = 0; t < GN; ++t) v[t] = *tile_elem<G>(sm, base + t, z);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+#pragma unroll
+      for (int t = 0; t < GN; ++t) {
+        if (t & (1 << r)) continue;
+        T b = v[t + (1 << r)];
+        // stage s = r + 1: jj = t mod 2^r
+        T tb;
+        if (r == 0) tb = twiddle_const<T, 1, 0>(b, inverse, tw, G::BX - 1);
+        else if (r == 1) {
+          if ((t & 1) == 0) tb = twiddle_const<T, 2, 0>(b, inverse, tw, G::BX - 2);
+          else tb = twiddle_const<T, 2, 1>(b, inverse, tw, G::BX - 2);
+        } else {
+          switch (t & 3) {
+            case 0: tb = twiddle_const<T, 3, 0>(b, inverse, tw, G::BX - 3); break;
+            case 1: tb = twiddle_const<T, 3, 1>(b, inverse, tw, G::BX - 3); break;
+            case 2: tb = twiddle_const<T, 3, 2>(b, inverse, tw, G::BX - 3); break;
+            default: tb = twiddle_const<T, 3, 3>(b, inverse, tw, G::BX - 3); break;
+          }
+        }
+        T a = v[t];
+        v[t].x = a.x + tb.x;
+        v[t].y = a.y + tb.y;
+        v[t + (1 << r)].x = a.x - tb.x;
+        v[t + (1 << r)].y = a.y - tb.y;
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < GN; ++t) *tile_elem<G>(sm, base + t, z) = v[t];
+  }
+}
+
+// Stages s0+1 .. s0+R (R <= 3) on every output row of a staged tile, in
+// registers: each thread takes groups of 2^R elements of one shared-memory
+// column, X = base + j + t 2^s0 (t < 2^R), which those R stages combine only
+// among themselves (the radix-2^R view of R consecutive radix-2 stages).
+template <class G, int NTHR, int R>
+__device__ __forceinline__ void dit_pass(uint4* sm, int s0, int inverse,
+                                         const typename Cplx<G::E>::T* tw) {
+  using T = typename Cplx<G::E>::T;
+  constexpr int GN = 1 << R;
+  const int groups = 1 << (G::BX + G::BZ - R);
+  for (int g = threadIdx.x; g < groups; g += NTHR) {
+    const int z = g & ((1 << G::BZ) - 1);
+    const int q = g >> G::BZ;
+    const int j = q & ((1 << s0) - 1);
+    const int base = (q >> s0) << (s0 + R);
+    T v[GN];
+#pragma unroll
+    for (int t = 0; t < GN; ++t) v[t] = *tile_elem<G>(sm, base + j + (t << s0), z);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int s = s0 + r + 1;
+      const int hmask = (1 << (s - 1)) - 1;
+#pragma unroll
+      for (int t = 0; t < GN; ++t) {
+        if (t & (1 << r)) continue;
+        const int jj = (j + (t << s0)) & hmask;
+        T w = tw[jj << (G::BX - s)];
+        if (inverse) w.y = -w.y;
+        butterfly(v[t], v[t + (1 << r)], w);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < GN; ++t) *tile_elem<G>(sm, base + j + (t << s0), z) = v[t];
+  }
+}
+
+// Stages 1..S on every output row of a staged tile (columns of sm), three
+// at a time: the first pass with compile-time twiddles, later ones from the
+// table.
 template <class G, int NTHR>
 __device__ __forceinline__ void dit_stages(uint4* sm, int S, int inverse,
                                            const typename Cplx<G::E>::T* tw) {
-  using T = typename Cplx<G::E>::T;
-  constexpr int NB = 1 << (G::BX + G::BZ - 1);  // butterflies per stage
-  for (int s = 1; s <= S; ++s) {
-    const int h = 1 << (s - 1);
-#pragma unroll 2
-    for (int u = threadIdx.x; u < NB; u += NTHR) {
-      const int z = u & ((1 << G::BZ) - 1);
-      const int p = u >> G::BZ;
-      const int j = p & (h - 1);
-      const int X0 = ((p >> (s - 1)) << s) + j;
-      T* pa = tile_elem<G>(sm, X0, z);
-      T* pb = tile_elem<G>(sm, X0 + h, z);
-      T w = tw[j << (G::BX - s)];
-      if (inverse) w.y = -w.y;
-      const T a = *pa, b = *pb;
-      T t;
-      t.x = b.x * w.x - b.y * w.y;
-      t.y = b.x * w.y + b.y * w.x;
-      T o0, o1;
-      o0.x = a.x + t.x;
-      o0.y = a.y + t.y;
-      o1.x = a.x - t.x;
-      o1.y = a.y - t.y;
-      *pa = o0;
-      *pb = o1;
-    }
+  if (S <= 0) return;
+  const int R0 = S >= 3 ? 3 : S;
+  if (R0 == 3) dit_first_pass<G, NTHR, 3>(sm, inverse, tw);
+  else if (R0 == 2) dit_first_pass<G, NTHR, 2>(sm, inverse, tw);
+  else dit_first_pass<G, NTHR, 1>(sm, inverse, tw);
+  __syncthreads();
+  int s0 = R0;
+  while (s0 < S) {
+    const int R = S - s0 >= 3 ? 3 : S - s0;
+    if (R == 3) dit_pass<G, NTHR, 3>(sm, s0, inverse, tw);
+    else if (R == 2) dit_pass<G, NTHR, 2>(sm, s0, inverse, tw);
+    else dit_pass<G, NTHR, 1>(sm, s0, inverse, tw);
+    s0 += R;
     __syncthreads();
   }
 }

@@ -582,3 +582,54 @@ def test_fused_fft_butterfly_indexing():
                         a, b = exp[:, base + j].copy(), exp[:, base + j + h] * w
                         exp[:, base + j], exp[:, base + j + h] = a + b, a - b
             assert np.allclose(got, exp, atol=1e-12)
+
+
+def test_fused_fft_register_passes():
+    """dit_pass: groups of 2^R elements X = base + j + t 2^s0 per column, R
+    stages in registers, passes of up to three stages -- same result as the
+    textbook stages, every element in exactly one group per pass."""
+    rng = np.random.default_rng(1)
+    for B in (3, 4, 5, 6):
+        BZ = B
+        table = np.exp(-2j * np.pi * np.arange(1 << (B - 1)) / (1 << B))
+        for S in range(0, B + 1):
+            cols = rng.normal(size=(1 << BZ, 1 << B)) + 1j * rng.normal(size=(1 << BZ, 1 << B))
+            got = cols.copy()
+            s0 = 0
+            while s0 < S:
+                R = min(3, S - s0)
+                seen = set()
+                for g in range(1 << (B + BZ - R)):
+                    z = g & ((1 << BZ) - 1)
+                    q = g >> BZ
+                    j = q & ((1 << s0) - 1)
+                    base = (q >> s0) << (s0 + R)
+                    Xs = [base + j + (t << s0) for t in range(1 << R)]
+                    assert all(0 <= X < (1 << B) for X in Xs)
+                    for X in Xs:
+                        assert (z, X) not in seen
+                        seen.add((z, X))
+                    v = [got[z, X] for X in Xs]
+                    for r in range(R):
+                        s = s0 + r + 1
+                        hmask = (1 << (s - 1)) - 1
+                        for t in range(1 << R):
+                            if t & (1 << r):
+                                continue
+                            jj = (j + (t << s0)) & hmask
+                            w = table[jj << (B - s)]
+                            a, b = v[t], v[t + (1 << r)] * w
+                            v[t], v[t + (1 << r)] = a + b, a - b
+                    for X, val in zip(Xs, v):
+                        got[z, X] = val
+                assert len(seen) == (1 << BZ) << B
+                s0 += R
+            exp = cols.copy()
+            for s in range(1, S + 1):
+                m, h = 1 << s, 1 << (s - 1)
+                for base in range(0, 1 << B, m):
+                    for j in range(h):
+                        w = np.exp(-2j * np.pi * j / m)
+                        a, b = exp[:, base + j].copy(), exp[:, base + j + h] * w
+                        exp[:, base + j], exp[:, base + j + h] = a + b, a - b
+            assert np.allclose(got, exp, atol=1e-12), (B, S)
