@@ -59,6 +59,8 @@ def parse_args():
     ap.add_argument("--batch-kmax", type=int, default=20)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-next", action="store_true")
+    ap.add_argument("--next-k", type=int, default=28,
+                    help="array size (log2) of the transposition / FFT-stage measurements")
     return ap.parse_args()
 
 
@@ -311,7 +313,7 @@ def run_brev(args):
     next_rows = None
     if not args.no_next:
         next_rows = bench_next(torch, brev, inputs, device, stream, sampler, reduce_max,
-                               barrier, peak)
+                               barrier, peak, k=args.next_k)
 
     # ------------------------------------------------------------ e2e
     e2e = None
@@ -407,7 +409,7 @@ def load_traffic(kernel_name, k, E, mode):
 
 
 def bench_next(torch, brev, inputs, device, stream, sampler, reduce_max, barrier, peak,
-               reps=5, warm=2):
+               reps=5, warm=2, k=28):
     """The widened rows: transpositions (square and narrow: the even-odd step
     and the perfect shuffle) and the paper's recursive method (three passes)
     against the one-pass tile kernel, all on 4 GiB arrays."""
@@ -430,30 +432,31 @@ def bench_next(torch, brev, inputs, device, stream, sampler, reduce_max, barrier
         return reduce_max(ea.elapsed_time(eb)) / reps
 
     out = {}
-    k, E = 28, 16
+    E = 16
+    h = k // 2
     src = torch.empty((1 << k) * E, dtype=torch.uint8, device=device)
     inputs.fill_torch(src, 28, "c128", chunk=1 << 26)
     dst = torch.empty_like(src)
     nbytes = 2 * src.numel()
-    for name, a, c in (("transpose_16384x16384_c128", 14, 14),
-                       ("even_odd_c128_k28", 27, 1), ("perfect_shuffle_c128_k28", 1, 27)):
+    for name, a, c in ((f"transpose_{1 << h}x{1 << (k - h)}_c128", h, k - h),
+                       (f"even_odd_c128_k{k}", k - 1, 1), (f"perfect_shuffle_c128_k{k}", 1, k - 1)):
         ms = timed(lambda: L.brev_transpose(dst.data_ptr(), src.data_ptr(), a, c, E, sh))
         out[name] = {"ms": round(ms, 4), "gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
                      "frac": round(nbytes / (ms * 1e-3) / 1e9 / peak, 4)}
-    ms = timed(lambda: L.brev_transpose(dst.data_ptr(), dst.data_ptr(), 14, 14, E, sh))
-    out["transpose_in_place_16384x16384_c128"] = {
+    ms = timed(lambda: L.brev_transpose(dst.data_ptr(), dst.data_ptr(), h, h, E, sh))
+    out[f"transpose_in_place_{1 << h}x{1 << h}_c128"] = {
         "ms": round(ms, 4), "gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
         "frac": round(nbytes / (ms * 1e-3) / 1e9 / peak, 4)}
     one = timed(lambda: L.brev_permute_to(dst.data_ptr(), dst.data_ptr(), k, E, sh))
     rec = timed(lambda: L.brev_permute_recursive(dst.data_ptr(), k, E, sh))
-    out["recursive_vs_one_pass_c128_k28"] = {
+    out[f"recursive_vs_one_pass_c128_k{k}"] = {
         "one_pass_ms": round(one, 4), "recursive_ms": round(rec, 4),
         "ratio": round(rec / one, 3),
         "one_pass_gbs": round(nbytes / (one * 1e-3) / 1e9, 1),
         "recursive_hbm_passes": 3}
     # bit reversal fused with the first DIT FFT stages vs the plain permutation
     for kind, E, S in (("c64", 8, 6), ("c128", 16, 5)):
-        k2 = 28
+        k2 = k
         x = torch.empty((1 << k2) * E, dtype=torch.uint8, device=device)
         inputs.fill_torch(x, 29, kind, chunk=1 << 26)
         y = torch.empty_like(x)
@@ -462,7 +465,7 @@ def bench_next(torch, brev, inputs, device, stream, sampler, reduce_max, barrier
         fused = timed(lambda: L.brev_fft_stages(y.data_ptr(), x.data_ptr(), k2, E, S, 0, sh))
         fused_ip = timed(lambda: L.brev_fft_stages(y.data_ptr(), y.data_ptr(), k2, E, S, 0, sh))
         flops = 5.0 * (1 << k2) * S  # radix-2 butterfly stage: 5 n flops
-        out[f"fft_stages_{kind}_k28_S{S}"] = {
+        out[f"fft_stages_{kind}_k{k2}_S{S}"] = {
             "permute_ms": round(plain, 4), "fused_ms": round(fused, 4),
             "fused_in_place_ms": round(fused_ip, 4),
             "fused_gbs": round(nb / (fused * 1e-3) / 1e9, 1),
