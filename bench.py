@@ -59,6 +59,8 @@ def parse_args():
     ap.add_argument("--batch-kmax", type=int, default=20)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-next", action="store_true")
+    ap.add_argument("--points-out", default=None,
+                    help="write per-point median times of the sweep to this JSON file")
     ap.add_argument("--next-k", type=int, default=28,
                     help="array size (log2) of the transposition / FFT-stage measurements")
     return ap.parse_args()
@@ -231,10 +233,41 @@ def run_brev(args):
     step_bytes = sum(p["bytes"] for p, _ in seq)
     names = [shape_name(brev, p["k"], p["E"], ip) for p, ip in seq]
     L = brev.lib()
-    for _ in range(args.warmup):
+    # Warm-up.  Its last steps bracket every launch with CUDA events: the
+    # per-kernel shares, the per-point table and the choice of the dominant
+    # kernel come from them, so that the timed steps carry events around the
+    # dominant kernel's launches only.
+    prof_steps = min(args.warmup, 2)
+    per_kernel = {}
+    per_point = {}
+    for w in range(args.warmup):
+        prof = w >= args.warmup - prof_steps
+        evw = []
         for p, ip in seq:
+            if prof:
+                ea = torch.cuda.Event(enable_timing=True)
+                eb = torch.cuda.Event(enable_timing=True)
+                ea.record(stream)
             launch_point(brev, p, ip, sh)
-    torch.cuda.synchronize(device)
+            if prof:
+                eb.record(stream)
+                evw.append((ea, eb))
+        torch.cuda.synchronize(device)
+        for i, ((p, ip), (ea, eb)) in enumerate(zip(seq, evw)):
+            ms = ea.elapsed_time(eb)
+            per_kernel[names[i]] = per_kernel.get(names[i], 0.0) + ms
+            key = f"{p['kind']}_{'ip' if ip else 'oop'}_k{p['k']}"
+            per_point.setdefault(key, {"ms": [], "bytes": p["bytes"], "k": p["k"], "E": p["E"],
+                                       "mode": "ip" if ip else "oop", "kernel": names[i],
+                                       "seq": i})
+            per_point[key]["ms"].append(ms)
+    total_kernel_ms = sum(per_kernel.values())
+    # dominant kernel = most device time; its roofline is read at its
+    # largest launch configuration (one fixed size per launch)
+    dom_name = max(per_kernel, key=per_kernel.get)
+    dom_pts = [v for v in per_point.values() if v["kernel"] == dom_name]
+    dom = max(dom_pts, key=lambda v: (v["k"], sum(v["ms"])))
+    dom_i = dom["seq"]
 
     try:
         gpu_id = "GPU-" + str(torch.cuda.get_device_properties(device).uuid)
@@ -244,9 +277,9 @@ def run_brev(args):
     sampler.start()
     time.sleep(0.3)
 
-    # per-launch events inside the timed region (roofline of each kernel)
-    evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-            for _ in seq] for _ in range(args.steps)]
+    # timed steps: events only around the dominant launch configuration
+    dom_evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     barrier()
@@ -254,10 +287,14 @@ def run_brev(args):
     w0 = time.time()
     t_start.record(stream)
     for s in range(args.steps):
-        for (p, ip), (ea, eb) in zip(seq, evs[s]):
-            ea.record(stream)
-            launch_point(brev, p, ip, sh)
-            eb.record(stream)
+        ea, eb = dom_evs[s]
+        for i, (p, ip) in enumerate(seq):
+            if i == dom_i:
+                ea.record(stream)
+                launch_point(brev, p, ip, sh)
+                eb.record(stream)
+            else:
+                launch_point(brev, p, ip, sh)
     t_end.record(stream)
     barrier()
     w1 = time.time()
@@ -266,25 +303,7 @@ def run_brev(args):
     ms_total = reduce_max(t_start.elapsed_time(t_end))
     ms_per_step = ms_total / args.steps
     value = whole_job_gbs(step_bytes * args.steps, ws, ms_total * 1e-3)
-
-    # per-kernel aggregates from the per-launch events
-    per_kernel = {}
-    per_point = {}
-    for s_ in range(args.steps):
-        for i, ((p, ip), (ea, eb)) in enumerate(zip(seq, evs[s_])):
-            ms = ea.elapsed_time(eb)
-            per_kernel[names[i]] = per_kernel.get(names[i], 0.0) + ms
-            key = f"{p['kind']}_{'ip' if ip else 'oop'}_k{p['k']}"
-            per_point.setdefault(key, {"ms": [], "bytes": p["bytes"], "k": p["k"], "E": p["E"],
-                                       "mode": "ip" if ip else "oop", "kernel": names[i]})
-            per_point[key]["ms"].append(ms)
-    total_kernel_ms = sum(per_kernel.values())
-    # dominant kernel = most device time; its roofline is read at its
-    # largest launch configuration (one fixed size per launch)
-    dom_name = max(per_kernel, key=per_kernel.get)
-    dom_pts = [v for v in per_point.values() if v["kernel"] == dom_name]
-    dom = max(dom_pts, key=lambda v: (v["k"], sum(v["ms"])))
-    dom_ms = statistics.mean(dom["ms"])
+    dom_ms = statistics.mean(ea.elapsed_time(eb) for ea, eb in dom_evs)
     achieved = dom["bytes"] / (dom_ms * 1e-3) / 1e9
     traffic = load_traffic(dom_name, dom["k"], dom["E"], dom["mode"])
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
@@ -293,11 +312,18 @@ def run_brev(args):
                 "launch": f"k={dom['k']} E={dom['E']} {dom['mode']}",
                 "bytes_per_launch": dom["bytes"],
                 "avg_launch_ms": round(dom_ms, 4),
-                "launches_timed": len(dom["ms"]),
+                "launches_timed": args.steps,
                 "peak_source": f"{peak_src} (copy bandwidth)",
                 "kernel_share_of_step": round(per_kernel[dom_name] / total_kernel_ms, 3),
+                "shares_from": f"{prof_steps} warm-up steps with events around every launch",
                 "nominal_gbs": round(info["nominal_gbs"], 1),
                 "frac_nominal": round(achieved / info["nominal_gbs"], 4)}
+    if args.points_out and rank == 0:
+        with open(args.points_out, "w") as fh:
+            json.dump({key: {"k": v["k"], "E": v["E"], "mode": v["mode"], "kernel": v["kernel"],
+                             "median_ms": statistics.median(v["ms"]),
+                             "gbs": v["bytes"] / (statistics.median(v["ms"]) * 1e-3) / 1e9}
+                       for key, v in per_point.items()}, fh, indent=0)
     large = {}
     for key, v in per_point.items():
         if v["k"] >= 26:
@@ -364,6 +390,7 @@ def run_brev(args):
             "frac_of_peak": round(value / ws / peak, 4),
             "frac_of_nominal": round(value / ws / info["nominal_gbs"], 4),
             "large_arrays_gbs": large,
+            "large_arrays_from": "warm-up steps with CUDA events around every launch",
             "batched": batched,
             "serving": serving,
             "transpositions_and_recursive": next_rows,

@@ -387,7 +387,10 @@ __device__ __forceinline__ void tile_inplace_body(char* data, int k, uint32_t q,
 // of it) or the identity ones (a plain matrix transposition).  Same layout
 // and swizzle as Geom; rows may be narrower than 128 bytes, so the swizzle
 // mask is clipped to the row width.
-constexpr int RT_BATCH = 4;  // loads in flight per thread per batch
+#ifndef BREV_RT_BATCH
+#define BREV_RT_BATCH 4
+#endif
+constexpr int RT_BATCH = BREV_RT_BATCH;  // loads in flight per thread per batch
 
 template <int E, int W, int NTHR, bool NC, bool REV>
 __device__ __forceinline__ void load_tiles_g(typename ChunkT<W>::type* sm, const char* src0,
@@ -467,12 +470,16 @@ __device__ __forceinline__ void store_tile_g(const typename ChunkT<W>::type* sm,
 // (pairs first, then self-paired tiles; as tile_inplace_body).
 template <int E, int W, int NTHR>
 __device__ __forceinline__ void tile_inplace_body_rt(char* data, int k, int b, uint32_t q,
-                                                     typename ChunkT<W>::type* sm) {
+                                                     typename ChunkT<W>::type* sm,
+                                                     int order = 0) {
   const int wy = k - 2 * b;
   const uint32_t npairs = count_lt(wy);
   uint32_t y, ry;
   int nt;
-  if (q < npairs) {
+  if (order == 1 && wy >= BLOCK_ORDER_MIN_W) {
+    blocked_unit(q, wy, y, ry);
+    nt = y == ry ? 1 : 2;
+  } else if (q < npairs) {
     y = unrank_lt(q, wy);
     ry = rev_bits(y, wy);
     nt = 2;

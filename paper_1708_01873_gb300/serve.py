@@ -348,11 +348,17 @@ class GpuBackend:
         import ctypes
         n = len(reqs)
         base = self.arena.data_ptr()
-        ptrs = (ctypes.c_void_p * n)(*[base + r.offset for r in reqs])
-        ks = (ctypes.c_int * n)(*[r.k for r in reqs])
-        es = (ctypes.c_int * n)(*[r.E for r in reqs])
         st = self.streams[s]
-        rc = self.L.brev_permute_batched_mixed(ptrs, ks, es, n, st.cuda_stream)
+        if n == 1:
+            # a batch of one: the single-array launch (no batch workspace)
+            r = reqs[0]
+            p = base + r.offset
+            rc = self.L.brev_permute_to(p, p, r.k, r.E, st.cuda_stream)
+        else:
+            ptrs = (ctypes.c_void_p * n)(*[base + r.offset for r in reqs])
+            ks = (ctypes.c_int * n)(*[r.k for r in reqs])
+            es = (ctypes.c_int * n)(*[r.E for r in reqs])
+            rc = self.L.brev_permute_batched_mixed(ptrs, ks, es, n, st.cuda_stream)
         if rc != 0:
             raise RuntimeError(self.brev.brev_last_error())
         ev = self._events.pop() if self._events else self.torch.cuda.Event(enable_timing=True)
