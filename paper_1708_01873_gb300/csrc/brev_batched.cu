@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "brev_device.cuh"
+#include "brev_device_rt.cuh"
 #include "brev_internal.h"
 
 namespace brev {

@@ -13,6 +13,7 @@
 #include <cmath>
 
 #include "brev_device.cuh"
+#include "brev_device_rt.cuh"
 #include "brev_internal.h"
 
 namespace brev {
@@ -48,6 +49,36 @@ __device__ __forceinline__ void unrank_upper(uint32_t q, uint32_t& tr, uint32_t&
   tr = q - (uint32_t)((uint64_t)col * (col - 1) / 2);
 }
 
+// The same units in blocked order (T = tiles per side, a multiple of 8):
+// 64 consecutive units cover an 8 x 8 block of tile pairs, so the tiles
+// (tr, tc) and their partners (tc, tr) both come in runs of 8 adjacent
+// tiles.  Off-diagonal blocks (bi < bj) first, 64 pairs each; then the
+// diagonal blocks, 28 pairs (r < c inside the block) and 8 diagonal tiles
+// each.
+__device__ __forceinline__ int blocked_upper(uint32_t q, uint32_t T, uint32_t& tr,
+                                             uint32_t& tc) {
+  const uint32_t Tb = T >> 3;
+  const uint64_t off = (uint64_t)Tb * (Tb - 1) / 2 * 64;
+  if (q < off) {
+    uint32_t bi, bj;
+    unrank_upper(q >> 6, bi, bj);
+    tr = (bi << 3) + ((q >> 3) & 7u);
+    tc = (bj << 3) + (q & 7u);
+    return 2;
+  }
+  const uint32_t q2 = (uint32_t)(q - off);
+  const uint32_t blk = q2 / 36u, u = q2 - blk * 36u;
+  if (u < 28u) {
+    uint32_t r, c;
+    unrank_upper(u, r, c);
+    tr = (blk << 3) + r;
+    tc = (blk << 3) + c;
+    return 2;
+  }
+  tr = tc = (blk << 3) + (u - 28u);
+  return 1;
+}
+
 template <int E, int W>
 __global__ void __launch_bounds__(TR_THREADS) k_transpose_inplace(char* data, int a, int b) {
   extern __shared__ uint4 smem_u4[];
@@ -57,7 +88,9 @@ __global__ void __launch_bounds__(TR_THREADS) k_transpose_inplace(char* data, in
   const uint32_t q = blockIdx.x;
   uint32_t tr, tc;
   int nt;
-  if (q < npairs) {
+  if (T >= 8) {
+    nt = blocked_upper(q, (uint32_t)T, tr, tc);
+  } else if (q < npairs) {
     unrank_upper(q, tr, tc);
     nt = 2;
   } else {

@@ -439,6 +439,26 @@ def test_transpose_oop_index_math(E):
             check_perm(n, loads, stores, transpose_src_of_dst(a, c))
 
 
+def blocked_upper(q, T):
+    Tb = T >> 3
+    off = Tb * (Tb - 1) // 2 * 64
+    if q < off:
+        bi, bj = unrank_upper(q >> 6)
+        return (bi << 3) + ((q >> 3) & 7), (bj << 3) + (q & 7)
+    q2 = q - off
+    blk, u = q2 // 36, q2 % 36
+    if u < 28:
+        r, c = unrank_upper(u)
+        return (blk << 3) + r, (blk << 3) + c
+    return (blk << 3) + (u - 28), (blk << 3) + (u - 28)
+
+
+def test_blocked_upper_covers_each_pair_once():
+    for T in (8, 16, 64):
+        seen = [blocked_upper(q, T) for q in range(T * (T + 1) // 2)]
+        assert sorted(seen) == sorted((r, c) for c in range(T) for r in range(c + 1))
+
+
 def unrank_upper(q):
     import math
     col = int((1.0 + math.sqrt(1.0 + 8.0 * q)) * 0.5)
@@ -463,7 +483,7 @@ def test_upper_triangle_unranking():
 @pytest.mark.parametrize("E", (16, 8, 4, 1))
 def test_transpose_inplace_index_math(E):
     lv = (16 // E).bit_length() - 1
-    for a in (0, 1, 2, 5, 7, 8):
+    for a in (0, 1, 2, 5, 7, 8, 9):
         b = min(a, TARGET_B[E])
         W = 16 if b >= lv else E
         Tn = 1 << (a - b)
@@ -471,15 +491,19 @@ def test_transpose_inplace_index_math(E):
         loads, stores = [], []
         npairs = Tn * (Tn - 1) // 2
         for q in range(npairs + Tn):
-            if q < npairs:
+            if Tn >= 8:
+                tr, tc = blocked_upper(q, Tn)
+                assert tr <= tc < Tn
+            elif q < npairs:
                 tr, tc = unrank_upper(q)
-                assert tr < tc < Tn
+            else:
+                tr = tc = q - npairs
+            if tr < tc:
                 A = (tr << (b + a)) + (tc << b)
                 B_ = (tc << (b + a)) + (tr << b)
                 emulate_g(E, W, 256, False, [A, B_], [B_, A], 1 << a, 1 << a, b, b, n,
                           loads, stores)
             else:
-                tr = tc = q - npairs
                 A = (tr << (b + a)) + (tc << b)
                 emulate_g(E, W, 256, False, [A], [A], 1 << a, 1 << a, b, b, n, loads, stores)
         if a:
