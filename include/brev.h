@@ -202,6 +202,65 @@ BREV_API brev_status brev_permute_recursive(void *data, int log2n, int elem_byte
 BREV_API brev_status brev_fft_stages(void *dst, const void *src, int log2n, int elem_bytes,
                                      int stages, int inverse, void *stream);
 
+/* ---------------------------------------------------------------- serving */
+
+/* A native serving loop (no counterpart in the paper): requests for the
+ * in-place permutation of arrays of different sizes arrive over time and
+ * are served by continuous batching.
+ *   - Admission: first in, first out, when a slot is free and a first-fit
+ *     pool over the caller's device arena can hold the request's
+ *     2^k * elem_bytes bytes (admission by free HBM, the pool's own
+ *     accounting).
+ *   - Launch: every loop iteration puts all admitted requests (at most
+ *     max_batch) into ONE launch -- single-array for one request, the
+ *     persistent batched kernel for more -- on an idle stream, round robin
+ *     over n_streams, so requests arriving while others run overlap with
+ *     them on the device.
+ *   - Completion: a CUDA event per batch; completion times are read on the
+ *     device clock and each request's memory and slot are released.
+ * The arena is a caller-owned device buffer (256-byte aligned); the server
+ * owns its streams and events. */
+typedef struct brev_server brev_server;
+typedef struct brev_server_config {
+    int max_slots; /* requests admitted at once */
+    int max_batch; /* requests per launch */
+    int n_streams; /* streams with a batch in flight, 1..64 */
+} brev_server_config;
+typedef struct brev_server_stats {
+    uint64_t offered, completed, batches, launches;
+    double p50_us, p99_us, max_us, mean_us; /* device completion - arrival */
+    double queue_p99_us;                    /* launch - arrival */
+    double req_per_s, gbs, wall_s;          /* gbs: 2 n E bytes per request / wall time */
+    uint64_t peak_pool_bytes;
+    int max_inflight;
+} brev_server_stats;
+typedef struct brev_server_request {
+    uint64_t offset; /* byte offset of the request's buffer in the arena */
+    int log2n, elem_bytes, batch;
+    double arrival_us, done_us; /* since the run started */
+} brev_server_request;
+
+BREV_API brev_status brev_server_create(const brev_server_config *cfg, void *arena,
+                                        uint64_t arena_bytes, brev_server **out);
+BREV_API void brev_server_destroy(brev_server *srv);
+
+/* Serve a seeded Poisson stream in the calling thread (after waiting for all
+ * earlier work on the device, so the arena may be written on any stream
+ * beforehand; the call returns when every request has completed):
+ * exponential gaps of
+ * mean 1/rate_per_s over `seconds`, k uniform in [k_min, k_max], element
+ * size uniform over elem_bytes[0..n_elem_bytes).  Each request permutes, in
+ * place, the arena bytes the pool gave it (whatever they hold).
+ * hold_results != 0 keeps every completed request's buffer reserved until
+ * the run ends, so that the arena afterwards holds all results (needs an
+ * arena large enough for the whole stream).  trace, if not NULL, receives
+ * up to trace_capacity per-request records in arrival order. */
+BREV_API brev_status brev_server_run_poisson(brev_server *srv, uint64_t seed, double rate_per_s,
+                                             double seconds, int k_min, int k_max,
+                                             const int *elem_bytes, int n_elem_bytes,
+                                             int hold_results, brev_server_request *trace,
+                                             uint64_t trace_capacity, brev_server_stats *out);
+
 /* ---------------------------------------------------------------- host path */
 
 /* End-to-end form for host buffers: permutes src_host (2^log2n elements)

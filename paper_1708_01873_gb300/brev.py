@@ -36,6 +36,27 @@ class DeviceInfo(ctypes.Structure):
                 ("name", ctypes.c_char * 96)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("max_slots", ctypes.c_int), ("max_batch", ctypes.c_int),
+                ("n_streams", ctypes.c_int)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("offered", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("batches", ctypes.c_uint64), ("launches", ctypes.c_uint64),
+                ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double),
+                ("max_us", ctypes.c_double), ("mean_us", ctypes.c_double),
+                ("queue_p99_us", ctypes.c_double), ("req_per_s", ctypes.c_double),
+                ("gbs", ctypes.c_double), ("wall_s", ctypes.c_double),
+                ("peak_pool_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_int)]
+
+
+class ServerRequest(ctypes.Structure):
+    _fields_ = [("offset", ctypes.c_uint64), ("log2n", ctypes.c_int),
+                ("elem_bytes", ctypes.c_int), ("batch", ctypes.c_int),
+                ("arrival_us", ctypes.c_double), ("done_us", ctypes.c_double)]
+
+
 SIGNATURES = {
     "brev_permute_to": (_i, [_vp, _vp, _i, _i, _vp]),
     "brev_permute": (_i, [_vp, _i, _i, _i, _vp]),
@@ -52,6 +73,11 @@ SIGNATURES = {
     "brev_permute_segments": (_i, [_vp, _i, _i, _i, _vp]),
     "brev_permute_recursive": (_i, [_vp, _i, _i, _vp]),
     "brev_fft_stages": (_i, [_vp, _vp, _i, _i, _i, _i, _vp]),
+    "brev_server_create": (_i, [ctypes.POINTER(ServerConfig), _vp, _u64, ctypes.POINTER(_vp)]),
+    "brev_server_destroy": (None, [_vp]),
+    "brev_server_run_poisson": (_i, [_vp, _u64, ctypes.c_double, ctypes.c_double, _i, _i, _ip, _i,
+                                     _i, ctypes.POINTER(ServerRequest), _u64,
+                                     ctypes.POINTER(ServerStats)]),
     "brev_tile_shape": (_i, [_i, _i, _i, _ip, _ip, _ip]),
     "brev_permute_shape": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _vp]),
     "brev_shape_count": (_i, [_i, _i]),
@@ -299,6 +325,38 @@ def brev_fft_stages(dst, src, stages: int, inverse: bool = False, stream=None) -
     _check(lib().brev_fft_stages(dst.data_ptr(), src.data_ptr(), _log2(src.numel()),
                                  src.element_size(), stages, int(bool(inverse)),
                                  _stream_handle(stream, src.device)), "brev_fft_stages")
+
+
+# ----------------------------------------------------------- serving --
+def brev_server_run_poisson(arena, seed: int, rate_per_s: float, seconds: float,
+                            k_range=(10, 24), elem_sizes=(4, 8, 16), max_slots: int = 256,
+                            max_batch: int = 256, n_streams: int = 4,
+                            hold_results: bool = False, trace: bool = False):
+    """Run the native serving loop over the device tensor ``arena`` for a
+    seeded Poisson stream; returns (stats dict, trace list or None)."""
+    cfg = ServerConfig(max_slots, max_batch, n_streams)
+    h = ctypes.c_void_p()
+    _check(lib().brev_server_create(ctypes.byref(cfg), arena.data_ptr(),
+                                    arena.numel() * arena.element_size(), ctypes.byref(h)),
+           "brev_server_create")
+    try:
+        es = (ctypes.c_int * len(elem_sizes))(*elem_sizes)
+        cap = int(rate_per_s * seconds * 1.2 + 1000) if trace else 0
+        tr = (ServerRequest * cap)() if trace else None
+        st = ServerStats()
+        _check(lib().brev_server_run_poisson(h, seed, rate_per_s, seconds, k_range[0],
+                                             k_range[1], es, len(elem_sizes),
+                                             int(bool(hold_results)), tr, cap,
+                                             ctypes.byref(st)), "brev_server_run_poisson")
+    finally:
+        lib().brev_server_destroy(h)
+    stats = {f: getattr(st, f) for f, _ in ServerStats._fields_}
+    recs = None
+    if trace:
+        recs = [{"offset": r.offset, "log2n": r.log2n, "elem_bytes": r.elem_bytes,
+                 "batch": r.batch, "arrival_us": r.arrival_us, "done_us": r.done_us}
+                for r in tr[:st.offered]]
+    return stats, recs
 
 
 # -------------------------------------------------------------- host --

@@ -56,3 +56,47 @@ def test_serving_workload_runs(brev_lib, cuda_device):
     assert out["completed"] > 5000
     assert out["p99_us"] >= out["p50_us"] > 0
     assert out["gpu_launches"] >= out["batches"]
+
+
+def test_native_server_results_equal_alone(brev_lib, oracle_lib, cuda_device):
+    """The native loop serves a Poisson stream in the mix (continuous
+    batching over 3 streams); with results held, every request's region of
+    the arena must equal the single-array permutation of that region's
+    initial bytes (and the oracle for the small ones)."""
+    arena = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    inputs.fill_torch(arena, 99, "u8", chunk=1 << 26)
+    initial = arena.clone()
+    torch.cuda.synchronize()
+    stats, trace = brev_lib.brev_server_run_poisson(
+        arena, seed=7, rate_per_s=6000.0, seconds=0.15, k_range=(4, 17),
+        elem_sizes=(4, 8, 16), max_slots=32, max_batch=12, n_streams=3,
+        hold_results=True, trace=True)
+    torch.cuda.synchronize()
+    assert stats["completed"] == stats["offered"] == len(trace) > 300
+    assert stats["batches"] < stats["completed"]   # requests were batched
+    spans = sorted((r["offset"], r["offset"] + (r["elem_bytes"] << r["log2n"])) for r in trace)
+    assert all(a[1] <= b[0] for a, b in zip(spans, spans[1:]))  # disjoint buffers
+    for i, r in enumerate(trace):
+        E, k, off = r["elem_bytes"], r["log2n"], r["offset"]
+        nb = E << k
+        src = initial[off:off + nb].view(DTYPE[E])
+        alone = torch.empty_like(src)
+        brev_lib.brev_permute_to(alone, src)
+        got = arena[off:off + nb].cpu().numpy()
+        assert_bytes_equal(got, alone.view(torch.uint8).cpu().numpy(), E,
+                           f"request {i} k={k} E={E}: mix vs alone")
+        if k <= 11:
+            exp = oracle_lib.brev_oop(initial[off:off + nb].cpu().numpy(), k, E)
+            assert_bytes_equal(got, exp, E, f"request {i}: vs oracle")
+        assert r["done_us"] >= r["arrival_us"]
+
+
+def test_native_server_production_mode(brev_lib, cuda_device):
+    arena = torch.empty(4 << 30, dtype=torch.uint8, device="cuda")
+    stats, _ = brev_lib.brev_server_run_poisson(arena, seed=5, rate_per_s=20000.0, seconds=0.5)
+    assert stats["completed"] == stats["offered"] > 8000
+    assert 0 < stats["p50_us"] <= stats["p99_us"] <= stats["max_us"]
+    assert stats["peak_pool_bytes"] <= arena.numel()
+    with pytest.raises(brev_lib.BrevError):   # hold mode that cannot fit: refused, no hang
+        brev_lib.brev_server_run_poisson(arena[: 64 << 20], seed=1, rate_per_s=20000.0,
+                                         seconds=0.2, k_range=(20, 22), hold_results=True)
