@@ -20,6 +20,10 @@
 
 namespace brev {
 
+#ifndef BREV_FFT_MIN_CTAS
+#define BREV_FFT_MIN_CTAS 5  // register budget for 5 resident CTAs per SM (measured best)
+#endif
+
 template <int E> struct Cplx;
 template <> struct Cplx<8> { using T = float2; using R = float; };
 template <> struct Cplx<16> { using T = double2; using R = double; };
@@ -187,7 +191,7 @@ __device__ __forceinline__ void dit_stages(uint4* sm, int S, int inverse,
 }
 
 template <int E, int B>
-__global__ void __launch_bounds__(Geom<E, 16, B, B>::THREADS)
+__global__ void __launch_bounds__(Geom<E, 16, B, B>::THREADS, BREV_FFT_MIN_CTAS)
     k_fft_oop(char* __restrict__ dst, const char* __restrict__ src, int k, int S,
               int inverse) {
   using G = Geom<E, 16, B, B>;
@@ -206,7 +210,7 @@ __global__ void __launch_bounds__(Geom<E, 16, B, B>::THREADS)
 }
 
 template <int E, int B>
-__global__ void __launch_bounds__(Geom<E, 16, B, B>::THREADS)
+__global__ void __launch_bounds__(Geom<E, 16, B, B>::THREADS, BREV_FFT_MIN_CTAS)
     k_fft_inplace(char* data, int k, int S, int inverse) {
   using G = Geom<E, 16, B, B>;
   using T = typename Cplx<E>::T;
