@@ -146,6 +146,13 @@ class ClockSampler:
                 self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
+            self.proc = None
+
+    # nvidia-smi's polling stalls CUDA calls of the serving loop's host
+    # thread (one stall of 50-80 ms per run of a few seconds, measured on
+    # GB300), so the latency sections run with the sampler stopped.
+    pause = stop
+    resume = start
 
     def summary(self):
         inside = [s for s in self.samples
@@ -353,22 +360,21 @@ def run_brev(args):
         for p in pts:  # release the sweep's buffers for the serving pool
             p["src"] = p["dst"] = None
         torch.cuda.empty_cache()
-        w0 = time.time()
+        sampler.pause()
         arena = torch.empty(16 << 30, dtype=torch.uint8, device=device)
         native, _ = brev.brev_server_run_poisson(arena, seed=5, rate_per_s=20000.0,
                                                  seconds=args.serve_seconds)
         del arena
         torch.cuda.empty_cache()
-        sampler.window(w0, time.time())
-        w1 = time.time()
         py = serve_poisson(seconds=min(args.serve_seconds, 5.0), rate=20000.0, seed=5,
                            pool_bytes=16 << 30, device=local)
-        sampler.window(w1, time.time())
+        sampler.resume()
         serving = {k: (round(v, 1) if isinstance(v, float) else v) for k, v in native.items()}
         serving["loop"] = "native C++ (brev_server_run_poisson)"
         serving["workload"] = ("Poisson arrivals, mean 50 us apart (20k req/s), k uniform in "
                                "[10,24], E uniform in {4,8,16}, seed 5; arena 16 GiB, 256 "
                                "slots, 4 streams; latency = device completion - arrival")
+        serving["clock_sampling"] = "paused (nvidia-smi polling stalls the host loop)"
         serving["python_loop"] = {k: py[k] for k in ("completed", "p50_us", "p99_us", "gbs",
                                                      "mean_batch")}
     sampler.stop()

@@ -237,7 +237,9 @@ typedef struct brev_server_stats {
 typedef struct brev_server_request {
     uint64_t offset; /* byte offset of the request's buffer in the arena */
     int log2n, elem_bytes, batch;
-    double arrival_us, done_us; /* since the run started */
+    double arrival_us, launch_us, done_us; /* since the run started; launch: host
+                                            * time of the enqueue, done: device
+                                            * completion */
 } brev_server_request;
 
 BREV_API brev_status brev_server_create(const brev_server_config *cfg, void *arena,

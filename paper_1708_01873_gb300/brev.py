@@ -54,7 +54,8 @@ class ServerStats(ctypes.Structure):
 class ServerRequest(ctypes.Structure):
     _fields_ = [("offset", ctypes.c_uint64), ("log2n", ctypes.c_int),
                 ("elem_bytes", ctypes.c_int), ("batch", ctypes.c_int),
-                ("arrival_us", ctypes.c_double), ("done_us", ctypes.c_double)]
+                ("arrival_us", ctypes.c_double), ("launch_us", ctypes.c_double),
+                ("done_us", ctypes.c_double)]
 
 
 SIGNATURES = {
@@ -354,7 +355,8 @@ def brev_server_run_poisson(arena, seed: int, rate_per_s: float, seconds: float,
     recs = None
     if trace:
         recs = [{"offset": r.offset, "log2n": r.log2n, "elem_bytes": r.elem_bytes,
-                 "batch": r.batch, "arrival_us": r.arrival_us, "done_us": r.done_us}
+                 "batch": r.batch, "arrival_us": r.arrival_us, "launch_us": r.launch_us,
+                 "done_us": r.done_us}
                 for r in tr[:st.offered]]
     return stats, recs
 

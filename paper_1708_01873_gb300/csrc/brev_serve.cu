@@ -369,6 +369,7 @@ brev_status brev_server_run_poisson(brev_server* srv, uint64_t seed, double rate
       trace[i].elem_bytes = reqs[i].E;
       trace[i].batch = reqs[i].batch;
       trace[i].arrival_us = reqs[i].arrival * 1e6;
+      trace[i].launch_us = reqs[i].launch * 1e6;
       trace[i].done_us = reqs[i].done * 1e6;
     }
   }

@@ -60,19 +60,21 @@ def test_serving_workload_runs(brev_lib, cuda_device):
 
 def test_native_server_results_equal_alone(brev_lib, oracle_lib, cuda_device):
     """The native loop serves a Poisson stream in the mix (continuous
-    batching over 3 streams); with results held, every request's region of
+    batching over 2 streams); with results held, every request's region of
     the arena must equal the single-array permutation of that region's
-    initial bytes (and the oracle for the small ones)."""
+    initial bytes (and the oracle for the small ones).  Arrivals 10 us apart
+    on average outpace a launch per request, so batches form (at a few
+    thousand requests per second every request is served alone)."""
     arena = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     inputs.fill_torch(arena, 99, "u8", chunk=1 << 26)
     initial = arena.clone()
     torch.cuda.synchronize()
     stats, trace = brev_lib.brev_server_run_poisson(
-        arena, seed=7, rate_per_s=6000.0, seconds=0.15, k_range=(4, 17),
-        elem_sizes=(4, 8, 16), max_slots=32, max_batch=12, n_streams=3,
+        arena, seed=7, rate_per_s=100000.0, seconds=0.015, k_range=(4, 17),
+        elem_sizes=(4, 8, 16), max_slots=32, max_batch=12, n_streams=2,
         hold_results=True, trace=True)
     torch.cuda.synchronize()
-    assert stats["completed"] == stats["offered"] == len(trace) > 300
+    assert stats["completed"] == stats["offered"] == len(trace) > 1000
     assert stats["batches"] < stats["completed"]   # requests were batched
     spans = sorted((r["offset"], r["offset"] + (r["elem_bytes"] << r["log2n"])) for r in trace)
     assert all(a[1] <= b[0] for a, b in zip(spans, spans[1:]))  # disjoint buffers
@@ -88,7 +90,8 @@ def test_native_server_results_equal_alone(brev_lib, oracle_lib, cuda_device):
         if k <= 11:
             exp = oracle_lib.brev_oop(initial[off:off + nb].cpu().numpy(), k, E)
             assert_bytes_equal(got, exp, E, f"request {i}: vs oracle")
-        assert r["done_us"] >= r["arrival_us"]
+        # arrival and launch on the host clock, done on the device clock
+        assert r["arrival_us"] <= r["launch_us"] <= r["done_us"] + 20.0
 
 
 def test_native_server_production_mode(brev_lib, cuda_device):
