@@ -335,6 +335,15 @@ BREV_API brev_status brev_get_device_info(brev_device_info *out);
  * entry points); lets callers count launches inside a timed region. */
 BREV_API uint64_t brev_launch_count(void);
 
+/* Number of times a CTA of the batched kernel gave up waiting for its own
+ * bulk copies into shared memory (about one second with the copies not
+ * complete), on the current device since the library was loaded.  Each
+ * such CTA stops early, so some arrays of that batch are left partly
+ * permuted; the count is 0 on a healthy device.  Waits for all earlier work
+ * on the device (a synchronous read).  Errors: BREV_ERR_INVALID_ARG (out is
+ * NULL), BREV_ERR_CUDA. */
+BREV_API brev_status brev_wait_timeouts(uint64_t *out);
+
 BREV_API const char *brev_status_string(brev_status s);
 /* Message of the last failing call on this thread ("" if none). */
 BREV_API const char *brev_last_error(void);

@@ -88,6 +88,7 @@ SIGNATURES = {
     "brev_reset_tuning": (None, []),
     "brev_get_device_info": (_i, [ctypes.POINTER(DeviceInfo)]),
     "brev_launch_count": (_u64, []),
+    "brev_wait_timeouts": (_i, [ctypes.POINTER(_u64)]),
     "brev_status_string": (_cp, [_i]),
     "brev_last_error": (_cp, []),
     "brev_version": (_i, []),
@@ -416,6 +417,14 @@ def brev_get_device_info() -> dict:
 
 def brev_launch_count() -> int:
     return int(lib().brev_launch_count())
+
+
+def brev_wait_timeouts() -> int:
+    """Bounded waits of the batched kernel that gave up on the current
+    device (0 on a healthy device; synchronises the device)."""
+    v = _u64(0)
+    _check(lib().brev_wait_timeouts(ctypes.byref(v)), "brev_wait_timeouts")
+    return int(v.value)
 
 
 def brev_status_string(status: int) -> str:

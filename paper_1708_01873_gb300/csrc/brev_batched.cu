@@ -5,19 +5,20 @@
 // self-paired tiles (square tiles of exponent b), or one unit for a small
 // array staged whole -- and consecutive units of one array are grouped into
 // tickets of `grain` units.  Persistent CTAs (a full wave: SMs x resident
-// CTAs) take tickets from a global counter with atomicAdd, find the owning
-// array by a warp-parallel search over the descriptors' first-ticket
-// indices, and run the units with the same device bodies as the
-// single-array kernels.  The only cross-CTA interaction is the ticket
-// counter; there are no spin waits.
+// CTAs) take tickets from a global counter with atomicAdd and find the
+// owning array by a warp-parallel search over the descriptors'
+// first-ticket indices.  The only cross-CTA interaction is the ticket
+// counter; inside a CTA, a producer warp and the consumer warps hand
+// shared-memory stages to each other through mbarriers, every wait
+// bounded (about a second, then counted in g_batched_wait_timeouts).
 #include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <new>
 #include <vector>
 
+#include "brev_async.cuh"
 #include "brev_device.cuh"
-#include "brev_device_rt.cuh"
 #include "brev_internal.h"
 
 namespace brev {
@@ -34,6 +35,10 @@ struct BatchDesc {
 };
 
 constexpr int BATCH_THREADS = 256;
+#ifndef BREV_BATCHED_TICKET_BYTES
+#define BREV_BATCHED_TICKET_BYTES 262144
+#endif
+constexpr unsigned long long BATCH_TICKET_BYTES = BREV_BATCHED_TICKET_BYTES;
 #ifndef BREV_BATCHED_MIN_CTAS
 #define BREV_BATCHED_MIN_CTAS 3  // register cap: 65536 / (256 * 3) = 85 per thread
 #endif
@@ -63,68 +68,257 @@ __device__ __forceinline__ int find_array(const BatchDesc* __restrict__ d, int c
   return lo;
 }
 
-// One body per element size with the tile exponent at run time, each a
-// separate (not inlined) function: the kernel's register count is then that
-// of the largest body, not of all bodies inlined side by side.
-template <int E>
-__device__ BREV_BATCHED_BODY_ATTR void run_tiles(char* ptr, int k, int b, unsigned u, uint4* sm) {
-  tile_inplace_body_rt<E, 16, BATCH_THREADS>(ptr, k, b, u, sm);
+// ----------------------------------------------- TMA-staged kernel --
+// Each unit's tiles are brought into shared memory by bulk asynchronous
+// copies (one per tile row of 2^b E contiguous bytes), issued by warp 0 and
+// completed on an mbarrier, while all warps store the previous unit: a
+// pipeline of BATCH_STAGES stages per CTA that keeps no loaded data in
+// registers.
+// Shared-memory rows are padded to 2^b E + 16 bytes, and row x of a tile
+// lands at row rev_b(x), so the bit reversal of the high field costs
+// nothing.  The store phase reads V = 16/E rows of one 16-byte column,
+// transposes the V x V block in registers and writes V output rows
+// rev_b(z); lanes are ordered so that each quarter-warp's 16-byte reads hit
+// eight different bank groups (row pitch / 16 is odd) and each warp writes
+// whole 128-byte lines.
+#ifndef BREV_BATCHED_STORE_UNROLL
+#define BREV_BATCHED_STORE_UNROLL 1
+#endif
+constexpr int BATCH_STORE_UNROLL = BREV_BATCHED_STORE_UNROLL;
+#ifndef BREV_BATCHED_STAGES
+#define BREV_BATCHED_STAGES 2
+#endif
+constexpr int BATCH_STAGES = BREV_BATCHED_STAGES;
+
+// Unit staged in one pipeline stage.  nt: 2 = tile pair, 1 = self-paired
+// tile, 0 = small array staged whole, -1 = no unit.
+struct StageInfo {
+  char* a;                    // tile y (the whole array when nt = 0)
+  char* r;                    // tile rev(y)
+  unsigned long long stride;  // tile row stride in bytes
+  int E, b, k, nt;
+};
+
+__host__ __device__ constexpr unsigned padded_row_bytes(int E, int b) {
+  return ((unsigned)E << b) + 16u;
 }
 
-template <int E>
-__device__ BREV_BATCHED_BODY_ATTR void run_small(char* ptr, int k, uint4* sm) {
-  small_body<E>(ptr, ptr, k, BATCH_THREADS, reinterpret_cast<typename ChunkT<E>::type*>(sm));
+// Shared-memory bytes one stage needs for a unit of the array (k, E, b).
+static __host__ unsigned stage_unit_bytes(int k, int E, int b) {
+  const unsigned raw = b == 0 ? ((unsigned)E << k) : 2u * (1u << b) * padded_row_bytes(E, b);
+  return (raw + 127u) & ~127u;
 }
 
-__device__ __forceinline__ void run_unit(const BatchDesc& d, unsigned u, uint4* sm) {
+// Wait timeouts of the bulk-copy pipeline since the library loaded (each
+// is one CTA that gave up on a copy after about a second).
+__device__ unsigned g_batched_wait_timeouts;
+
+// Producer warp: stage unit u of array d into `buf`.  Lane 0 publishes
+// the unit's description in `info`, then arrives on `full` with the
+// unit's byte count (the arrival releases the description to the
+// consumers, who read it after the phase completes); all lanes then issue
+// the row copies, which complete on `full`.
+__device__ __forceinline__ void issue_unit(const BatchDesc& d, unsigned u, StageInfo* info,
+                                           unsigned char* buf, uint64_t* full) {
+  const int lane = threadIdx.x & 31;
+  StageInfo s;
+  s.E = d.E;
+  s.b = d.b;
+  s.k = d.k;
   if (d.b == 0) {
-    switch (d.E) {
-      case 16: run_small<16>(d.ptr, d.k, sm); break;
-      case 8: run_small<8>(d.ptr, d.k, sm); break;
-      case 4: run_small<4>(d.ptr, d.k, sm); break;
+    const uint32_t bytes = (uint32_t)d.E << d.k;
+    s.a = s.r = d.ptr;
+    s.stride = 0;
+    s.nt = 0;
+    if (lane == 0) {
+      *info = s;
+      mbar_arrive_expect_tx(full, bytes);
+      bulk_g2s(buf, d.ptr, bytes, full);
     }
     return;
   }
-  switch (d.E) {
-    case 16: run_tiles<16>(d.ptr, d.k, d.b, u, sm); break;
-    case 8: run_tiles<8>(d.ptr, d.k, d.b, u, sm); break;
-    case 4: run_tiles<4>(d.ptr, d.k, d.b, u, sm); break;
+  const int b = d.b, wy = d.k - 2 * b;
+  const uint32_t npairs = count_lt(wy);
+  uint32_t y, ry;
+  if (u < npairs) {
+    y = unrank_lt(u, wy);
+    ry = rev_bits(y, wy);
+    s.nt = 2;
+  } else {
+    y = unrank_self(u - npairs, wy);
+    ry = y;
+    s.nt = 1;
+  }
+  const uint32_t rowb = (uint32_t)d.E << b;
+  const uint32_t pitch = padded_row_bytes(d.E, b);
+  const int rows = 1 << b;
+  s.stride = (unsigned long long)d.E << (d.k - b);
+  s.a = d.ptr + ((uint64_t)y << b) * d.E;
+  s.r = d.ptr + ((uint64_t)ry << b) * d.E;
+  if (lane == 0) {
+    *info = s;
+    mbar_arrive_expect_tx(full, (uint32_t)s.nt * rows * rowb);
+  }
+  __syncwarp();
+  for (int q = lane; q < s.nt * rows; q += 32) {
+    const int t = q >> b, x = q & (rows - 1);
+    bulk_g2s(buf + (uint32_t)t * rows * pitch + rev_bits((uint32_t)x, b) * pitch,
+             (t ? s.r : s.a) + (uint64_t)x * s.stride, rowb, full);
   }
 }
 
-__global__ void __launch_bounds__(BATCH_THREADS, BREV_BATCHED_MIN_CTAS)
+// Store one staged 2^b x 2^b tile (rows at pitch P, row X = rev(x)) into
+// the destination tile: output row rev(z), column X.
+template <int E>
+__device__ __forceinline__ void store_staged_tile(const unsigned char* sm, char* dst,
+                                                  uint64_t stride, int b, uint32_t pitch) {
+  constexpr int V = 16 / E;
+  constexpr int LOG_V = ilog2c(V);
+  const int log_c = b - LOG_V;
+  const int cmask = (1 << log_c) - 1;
+  const int units = 1 << (2 * log_c);
+#pragma unroll BATCH_STORE_UNROLL
+  for (int q = threadIdx.x; q < units; q += BATCH_THREADS) {
+    const int cl = q & (V - 1);
+    const int rest = q >> LOG_V;
+    const int d = rest & cmask;
+    const int c = ((rest >> log_c) << LOG_V) | cl;
+    uint4 blk[V], out[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j)
+      blk[j] = *reinterpret_cast<const uint4*>(sm + (uint32_t)(d * V + j) * pitch + c * 16);
+    xpose<E, 16>(blk, out);
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      const uint32_t Z = rev_bits((uint32_t)(c * V + e), b);
+      gstore<16>(dst + (uint64_t)Z * stride + (unsigned)d * 16, out[e]);
+    }
+  }
+}
+
+template <int E>
+__device__ BREV_BATCHED_BODY_ATTR void store_staged_unit(const unsigned char* sm, char* a,
+                                                        char* r, uint64_t stride, int b, int k,
+                                                        int nt) {
+  using C = typename ChunkT<E>::type;
+  if (nt == 0) {  // small array: out[j] = in[rev j], coalesced writes
+    const uint32_t n = 1u << k;
+    for (uint32_t j = threadIdx.x; j < n; j += BATCH_THREADS)
+      gstore<E>(a + (uint64_t)j * E,
+                *reinterpret_cast<const C*>(sm + (size_t)rev_bits(j, k) * E));
+    return;
+  }
+  const uint32_t pitch = padded_row_bytes(E, b);
+  store_staged_tile<E>(sm, r, stride, b, pitch);  // tile y's data into tile rev(y)
+  if (nt == 2) store_staged_tile<E>(sm + ((uint32_t)pitch << b), a, stride, b, pitch);
+}
+
+// Warps 0..7 store (consumers, threads 0..255); warp 8 is the producer.
+// Stage p serves units p, p + S, p + 2S, ... (S = BATCH_STAGES).  full[p]
+// completes when the unit's copies have landed (one producer arrival plus
+// the bytes); empty[p] completes when all 8 consumer warps have read the
+// stage.  No block-wide barrier after the set-up: each consumer warp moves
+// on as soon as its own share of a unit is stored.
+constexpr int BATCH_CONSUMER_WARPS = BATCH_THREADS / 32;
+constexpr int BATCH_BLOCK = BATCH_THREADS + 32;
+
+__global__ void __launch_bounds__(BATCH_BLOCK, BREV_BATCHED_MIN_CTAS)
     k_batched(const BatchDesc* __restrict__ desc, int count, unsigned long long tickets,
-              unsigned long long* ticket_ctr) {
-  extern __shared__ uint4 smem_u4[];
-  __shared__ unsigned long long s_next;
-  __shared__ int s_array;
-  if (threadIdx.x == 0) s_next = atomicAdd(ticket_ctr, 1ull);
-  __syncthreads();
-  unsigned long long t = s_next;
-  while (t < tickets) {
-    if (threadIdx.x < 32) {
-      const int a = find_array(desc, count, t);
-      if (threadIdx.x == 0) s_array = a;
+              unsigned long long* ticket_ctr, unsigned stage_bytes) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full[BATCH_STAGES], empty[BATCH_STAGES];
+  __shared__ StageInfo info[BATCH_STAGES];
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid == 0) {
+    for (int i = 0; i < BATCH_STAGES; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], BATCH_CONSUMER_WARPS);
     }
-    __syncthreads();  // s_array written; every thread has read s_next (= t)
-    // take the next ticket now: the atomic's round trip overlaps this
-    // ticket's units (its value is read after their barriers)
-    if (threadIdx.x == 0) s_next = atomicAdd(ticket_ctr, 1ull);
-    const BatchDesc d = desc[s_array];
-    const unsigned first = (unsigned)(t - d.first_ticket) * d.grain;
-    const unsigned last = min(first + d.grain, d.units);
-    for (unsigned u = first; u < last; ++u) {
-      run_unit(d, u, smem_u4);
-      __syncthreads();  // the next unit reuses the shared-memory tiles
+    mbar_init_fence();
+  }
+  __syncthreads();  // barriers initialised
+
+  if (tid >= BATCH_THREADS) {
+    // ---- producer warp: tickets -> units -> bulk copies
+    int a = -1;
+    unsigned u = 0, ulast = 0;
+    BatchDesc d{};
+    // lane 0 holds the next ticket's number; its atomic is read only when
+    // the current ticket runs out
+    unsigned long long pending = 0;
+    if (lane == 0) pending = atomicAdd(ticket_ctr, 1ull);
+    unsigned i = 0;
+    bool ok = true;
+#pragma unroll 1
+    for (;; ++i) {
+      const int st = i % BATCH_STAGES;
+      if (i >= BATCH_STAGES) {  // wait until every consumer warp has read the stage
+        ok = mbar_wait_bounded(&empty[st], (i / BATCH_STAGES - 1) & 1);
+        if (!ok) break;
+        fence_proxy_async_smem();
+      }
+      bool more = true;
+      if (a >= 0 && u + 1 < ulast) {
+        ++u;
+      } else {
+        const unsigned long long t = __shfl_sync(0xffffffffu, pending, 0);
+        if (t >= tickets) {
+          more = false;
+        } else {
+          a = find_array(desc, count, t);
+          d = desc[a];
+          u = (unsigned)(t - d.first_ticket) * d.grain;
+          ulast = min(u + d.grain, d.units);
+          if (lane == 0) pending = atomicAdd(ticket_ctr, 1ull);
+        }
+      }
+      if (!more) {  // end marker: a phase with no bytes
+        if (lane == 0) {
+          info[st].nt = -1;
+          mbar_arrive(&full[st]);
+        }
+        break;
+      }
+      issue_unit(d, u, &info[st], smem + (size_t)st * stage_bytes, &full[st]);
     }
-    t = s_next;  // written before the barrier that ended the last unit
+    if (!ok && lane == 0) atomicAdd(&g_batched_wait_timeouts, 1u);
+    // the copies of the units still possibly in flight must land before the
+    // CTA may exit: units i-S+1 .. i-1, and unit i-S too after a timeout
+    // (after the end marker, unit i-S's stage was released and its barrier
+    // has moved on to the marker's phase)
+    const unsigned back = ok ? BATCH_STAGES - 1 : BATCH_STAGES;
+    for (unsigned m = 1; m <= back && m <= i; ++m) {
+      const unsigned j = i - m;
+      mbar_wait_bounded(&full[j % BATCH_STAGES], (j / BATCH_STAGES) & 1);
+    }
+    return;
+  }
+
+  // ---- consumer warps
+#pragma unroll 1
+  for (unsigned i = 0;; ++i) {
+    const int st = i % BATCH_STAGES;
+    if (!mbar_wait_bounded(&full[st], (i / BATCH_STAGES) & 1)) {
+      if (lane == 0) atomicAdd(&g_batched_wait_timeouts, 1u);
+      return;
+    }
+    const StageInfo s = info[st];
+    if (s.nt < 0) return;
+    const unsigned char* buf = smem + (size_t)st * stage_bytes;
+    switch (s.E) {
+      case 16: store_staged_unit<16>(buf, s.a, s.r, s.stride, s.b, s.k, s.nt); break;
+      case 8: store_staged_unit<8>(buf, s.a, s.r, s.stride, s.b, s.k, s.nt); break;
+      case 4: store_staged_unit<4>(buf, s.a, s.r, s.stride, s.b, s.k, s.nt); break;
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[st]);
   }
 }
 
 // ------------------------------------------------------------------ host --
 
-// Tile exponents with a body in run_unit (at most 16 KiB tiles, so the
-// kernel keeps several CTAs per SM).
+// Tile exponents the batched kernel stages (at most 16 KiB tiles, so two
+// stages of a tile pair leave room for three CTAs per SM).
 static bool batched_shape_ok(int E, int b) {
   switch (E) {
     case 16: return b == 0 || (b >= 3 && b <= 5);
@@ -150,7 +344,7 @@ static int batched_b(int k, int E) {
 struct BatchPlanData {
   std::vector<BatchDesc> desc;
   unsigned long long tickets = 0;
-  unsigned smem = 0;
+  unsigned stage_bytes = 0;  // shared memory of one pipeline stage
   std::vector<BatchItem> fallback;  // arrays run with single-array launches
 };
 
@@ -179,15 +373,15 @@ static brev_status build_batch(const BatchItem* items, int count, BatchPlanData*
     if (b == 0) {
       d.units = 1;
       unit_bytes = (unsigned long long)it.E << it.k;
-      out->smem = std::max<unsigned>(out->smem, (unsigned)unit_bytes);
     } else {
       const int w = it.k - 2 * b;
       d.units = count_lt(w) + count_self(w);
       unit_bytes = 2ull * ((unsigned long long)it.E << (2 * b));
-      out->smem = std::max<unsigned>(out->smem, (unsigned)unit_bytes);
     }
-    // about 256 KiB of tile data per ticket
-    const unsigned long long g = std::max<unsigned long long>(1, 262144ull / unit_bytes);
+    out->stage_bytes = std::max(out->stage_bytes, stage_unit_bytes(it.k, it.E, b));
+    // about BATCH_TICKET_BYTES of tile data per ticket
+    const unsigned long long g =
+        std::max<unsigned long long>(1, BATCH_TICKET_BYTES / unit_bytes);
     d.grain = (unsigned)std::min<unsigned long long>(g, d.units);
     tmp.push_back({d, (unsigned long long)it.E << it.k});
   }
@@ -208,13 +402,33 @@ static brev_status build_batch(const BatchItem* items, int count, BatchPlanData*
 
 static int batched_grid(unsigned smem) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched, BATCH_THREADS, smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched, BATCH_BLOCK, smem) !=
           cudaSuccess ||
       per_sm < 1) {
     cudaGetLastError();
     per_sm = 1;
   }
   return per_sm * current_device_sm_count();
+}
+
+// Launch the persistent kernel over `count` descriptors already on the
+// device (ticket counter zeroed in stream order before it).
+static brev_status launch_batched_kernel(const BatchDesc* d_desc, int count,
+                                         unsigned long long tickets,
+                                         unsigned long long* d_ticket, unsigned stage_bytes,
+                                         cudaStream_t stream) {
+  const unsigned smem = BATCH_STAGES * stage_bytes;
+  cudaError_t e = ensure_smem((const void*)k_batched, smem);
+  if (e != cudaSuccess) return cuda_error(e, "shared-memory limit of the batched kernel");
+  const int grid =
+      (int)std::min<unsigned long long>((unsigned long long)batched_grid(smem), tickets);
+  void* args[] = {(void*)&d_desc, (void*)&count, (void*)&tickets, (void*)&d_ticket,
+                  (void*)&stage_bytes};
+  e = cudaLaunchKernel((const void*)k_batched, dim3(grid), dim3(BATCH_BLOCK), args, smem,
+                       stream);
+  if (e != cudaSuccess) return cuda_error(e, "batched kernel launch");
+  note_launch();
+  return BREV_OK;
 }
 
 // Enqueue the ticket reset, the persistent kernel and the per-array
@@ -224,17 +438,9 @@ static brev_status enqueue_batch(const BatchPlanData& p, const BatchDesc* d_desc
   if (!p.desc.empty()) {
     cudaError_t e = cudaMemsetAsync(d_ticket, 0, sizeof(unsigned long long), stream);
     if (e != cudaSuccess) return cuda_error(e, "ticket reset");
-    e = ensure_smem((const void*)k_batched, p.smem);
-    if (e != cudaSuccess) return cuda_error(e, "shared-memory limit of the batched kernel");
-    const int grid = (int)std::min<unsigned long long>(
-        (unsigned long long)batched_grid(p.smem), p.tickets);
-    int count = (int)p.desc.size();
-    unsigned long long tickets = p.tickets;
-    void* args[] = {(void*)&d_desc, (void*)&count, (void*)&tickets, (void*)&d_ticket};
-    e = cudaLaunchKernel((const void*)k_batched, dim3(grid), dim3(BATCH_THREADS), args, p.smem,
-                         stream);
-    if (e != cudaSuccess) return cuda_error(e, "batched kernel launch");
-    note_launch();
+    brev_status s = launch_batched_kernel(d_desc, (int)p.desc.size(), p.tickets, d_ticket,
+                                          p.stage_bytes, stream);
+    if (s != BREV_OK) return s;
   }
   for (const BatchItem& it : p.fallback) {
     brev_status s = launch_single(it.ptr, it.ptr, it.k, it.E, stream);
@@ -356,6 +562,15 @@ extern "C" brev_status brev_plan_create(void* const* ptr_array, const int* log2n
   return BREV_OK;
 }
 
+extern "C" brev_status brev_wait_timeouts(uint64_t* out) {
+  if (!out) return set_error(BREV_ERR_INVALID_ARG, "out is NULL");
+  unsigned v = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(&v, g_batched_wait_timeouts, sizeof(v));
+  if (e != cudaSuccess) return cuda_error(e, "reading the wait-timeout counter");
+  *out = v;
+  return BREV_OK;
+}
+
 extern "C" brev_status brev_plan_launch(brev_plan* plan, void* stream) {
   if (!plan || !plan->exec) return set_error(BREV_ERR_INVALID_ARG, "invalid plan");
   cudaError_t e = cudaGraphLaunch(plan->exec, (cudaStream_t)stream);
@@ -469,7 +684,7 @@ extern "C" brev_status brev_permute_batched_noalloc(void* const* ptr_array,
   }
   // descriptors (the same decomposition as brev_permute_batched_mixed)
   int nd = 0, nf = 0;
-  unsigned smem = 0;
+  unsigned stage_bytes = 0;
   for (int i = 0; i < count; ++i) {
     const BatchItem it{ptr_array[i], log2n_array[i], elem_bytes_array[i]};
     if (it.k <= 1) continue;
@@ -493,8 +708,9 @@ extern "C" brev_status brev_permute_batched_noalloc(void* const* ptr_array,
       d.units = count_lt(w) + count_self(w);
       unit_bytes = 2ull * ((unsigned long long)it.E << (2 * b));
     }
-    smem = std::max<unsigned>(smem, (unsigned)unit_bytes);
-    const unsigned long long g = std::max<unsigned long long>(1, 262144ull / unit_bytes);
+    stage_bytes = std::max(stage_bytes, stage_unit_bytes(it.k, it.E, b));
+    const unsigned long long g =
+        std::max<unsigned long long>(1, BATCH_TICKET_BYTES / unit_bytes);
     d.grain = (unsigned)std::min<unsigned long long>(g, d.units);
     h.desc[nd] = d;
     h.bytes[nd] = (unsigned long long)it.E << it.k;
@@ -524,19 +740,8 @@ extern "C" brev_status brev_permute_batched_noalloc(void* const* ptr_array,
     if (e != cudaSuccess) return cuda_error(e, "descriptor upload (no-alloc)");
     e = cudaMemsetAsync(d_ticket, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return cuda_error(e, "ticket reset (no-alloc)");
-    if (smem > 48 * 1024) {
-      e = cudaFuncSetAttribute((const void*)k_batched,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return cuda_error(e, "shared-memory limit (no-alloc)");
-    }
-    const int grid = (int)std::min<unsigned long long>((unsigned long long)batched_grid(smem),
-                                                       tickets);
-    int cnt = nd;
-    void* args[] = {(void*)&d_desc, (void*)&cnt, (void*)&tickets, (void*)&d_ticket};
-    e = cudaLaunchKernel((const void*)k_batched, dim3(grid), dim3(BATCH_THREADS), args, smem,
-                         st);
-    if (e != cudaSuccess) return cuda_error(e, "batched kernel launch (no-alloc)");
-    note_launch();
+    s = launch_batched_kernel(d_desc, nd, tickets, d_ticket, stage_bytes, st);
+    if (s != BREV_OK) return s;
   }
   for (int i = 0; i < nf; ++i) {
     brev_status s = launch_single(h.fallback[i].ptr, h.fallback[i].ptr, h.fallback[i].k,

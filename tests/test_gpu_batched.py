@@ -32,6 +32,7 @@ def test_batched_mixed_vs_oracle(brev_lib, oracle_lib, cuda_device):
     assert brev_lib.brev_launch_count() - c0 == 1  # one persistent launch
     for a, e, (k, E, _) in zip(arrays, _expect(oracle_lib, hosts), hosts):
         assert_bytes_equal(to_bytes(a), e, E, f"batched k={k} E={E}")
+    assert brev_lib.brev_wait_timeouts() == 0  # no CTA gave up on its copies
 
 
 def test_batched_single_elem_size_api(brev_lib, oracle_lib, cuda_device):
@@ -160,6 +161,7 @@ def test_batched_config4_full_size(brev_lib, oracle_lib, cuda_device):
         inputs.fill_torch(ref, 40000 + i, KIND[E], chunk=1 << 26)
         assert torch.equal(arrays[i].view(torch.uint8), ref), f"array {i} after two replays"
     plan.close()
+    assert brev_lib.brev_wait_timeouts() == 0
 
 
 def test_host_path(brev_lib, oracle_lib, cuda_device):

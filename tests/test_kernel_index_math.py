@@ -275,13 +275,108 @@ def test_element_wide_index_math(E):
         check_result(k, loads, stores)
 
 
-def test_batched_thread_count_index_math():
-    """The batched kernel runs the in-place bodies with 256 threads even when
-    the tile has fewer units (guards on q and u)."""
-    for E, b in ((16, 3), (16, 5), (8, 4), (4, 5), (4, 7)):
-        k = 2 * b + 2
-        G, loads, stores, _ = run_inplace(E, 16, b, k, nthr=256)
+def batched_stage_bytes(k, E, b):
+    raw = (E << k) if b == 0 else 2 * (1 << b) * ((E << b) + 16)
+    return (raw + 127) & ~127
+
+
+def emulate_staged_unit(E, b, k, u, nthr=256):
+    """Replay one unit of the TMA-staged batched kernel: the bulk copies
+    warp 0 issues (row x of each tile to padded row rev(x)) and the store
+    phase of all threads.  Returns (copied source elements, stores as
+    (destination element, source element), read-slot conflicts)."""
+    n = 1 << k
+    stage = batched_stage_bytes(k, E, b)
+    smem = {}  # byte offset of an element in the stage -> source element
+    loads, stores, conflicts = [], [], 0
+    if b == 0:
+        nbytes = E << k
+        assert nbytes % 16 == 0 and nbytes <= stage
+        for i in range(n):
+            smem[i * E] = i
+            loads.append(i)
+        for j in range(n):
+            stores.append((j, smem[brev(j, k) * E]))
+        return loads, stores, 0
+    wy = k - 2 * b
+    npairs = count_lt(wy)
+    if u < npairs:
+        y = unrank_lt(u, wy)
+        ry, nt = brev(y, wy), 2
+    else:
+        y = unrank_self(u - npairs, wy)
+        ry, nt = y, 1
+    rowb, rows = E << b, 1 << b
+    pitch = rowb + 16
+    stride = E << (k - b)
+    a_off, r_off = (y << b) * E, (ry << b) * E
+    tx = 0
+    for q in range(nt * rows):
+        t, x = q >> b, q & (rows - 1)
+        dst = t * rows * pitch + brev(x, b) * pitch
+        src = (r_off if t else a_off) + x * stride
+        assert dst % 16 == 0 and src % 16 == 0 and rowb % 16 == 0
+        assert 0 <= dst and dst + rowb <= stage and 0 <= src and src + rowb <= n * E
+        for o in range(0, rowb, E):
+            assert dst + o not in smem
+            smem[dst + o] = (src + o) // E
+            loads.append((src + o) // E)
+        tx += rowb
+    assert tx == nt * rows * rowb  # the byte count lane 0 expects
+    V = 16 // E
+    log_v = V.bit_length() - 1
+    log_c = b - log_v
+    cmask = (1 << log_c) - 1
+    units = 1 << (2 * log_c)
+    for t, dst_tile in ((0, r_off), (1, a_off))[:nt]:
+        base = t * rows * pitch
+        reads = {}
+        for q in range(units):
+            cl = q & (V - 1)
+            rest = q >> log_v
+            d = rest & cmask
+            c = ((rest >> log_c) << log_v) | cl
+            blk = []
+            for j in range(V):
+                addr = base + (d * V + j) * pitch + c * 16
+                assert addr % 16 == 0 and addr + 16 <= stage
+                blk.append([smem[addr + e * E] for e in range(V)])
+                reads.setdefault((q // 32, j), []).append((q % nthr, addr // 16))
+            for e in range(V):
+                Z = brev(c * V + e, b)
+                g = dst_tile + Z * stride + d * 16
+                assert g % 16 == 0 and g + 16 <= n * E
+                for j in range(V):
+                    stores.append((g // E + j, blk[j][e]))
+        conflicts += sum(_wavefront_conflicts(sl, 16) for sl in reads.values())
+    return loads, stores, conflicts
+
+
+BATCHED_SHAPES = {16: (3, 4, 5), 8: (4, 5), 4: (5, 6)}
+BATCHED_BMIN = {16: 3, 8: 4, 4: 5}
+
+
+@pytest.mark.parametrize("E", sorted(BATCHED_SHAPES))
+def test_batched_staged_index_math(E):
+    """TMA-staged batched kernel: copies in bounds, 16-byte aligned and
+    counted in the expected bytes; every staged chunk read once per tile
+    without bank conflicts; every element moved once to rev(i)."""
+    cases = [(k, 0) for k in range(2, 2 * BATCHED_BMIN[E])]
+    cases += [(k, b) for b in BATCHED_SHAPES[E] for k in range(2 * b, 2 * b + 4)
+              if k <= 17]
+    for k, b in cases:
+        units = 1 if b == 0 else count_lt(k - 2 * b) + count_self(k - 2 * b)
+        loads, stores, conf = [], [], 0
+        for u in range(units):
+            lo, st, c = emulate_staged_unit(E, b, k, u)
+            loads += lo
+            stores += st
+            conf += c
         check_result(k, loads, stores)
+        assert conf == 0, (E, b, k)
+    # two stages of the largest unit leave room for three CTAs per SM
+    worst = max(batched_stage_bytes(2 * b, E, b) for b in BATCHED_SHAPES[E])
+    assert 3 * (2 * worst + 1024 + 128) <= 228 * 1024
 
 
 def test_unranking_enumerates_pairs_and_palindromes():
@@ -657,3 +752,116 @@ def test_fused_fft_register_passes():
                         a, b = exp[:, base + j].copy(), exp[:, base + j + h] * w
                         exp[:, base + j], exp[:, base + j + h] = a + b, a - b
             assert np.allclose(got, exp, atol=1e-12), (B, S)
+
+
+class _MBar:
+    """mbarrier phase semantics: a phase completes when its pending
+    arrivals reach 0 and its transaction bytes are all in; try_wait(P) is
+    true while the barrier's current phase parity differs from P."""
+
+    def __init__(self, count):
+        self.count, self.pending, self.tx, self.completed = count, count, 0, 0
+
+    def _check(self):
+        if self.pending == 0 and self.tx == 0:
+            self.completed += 1
+            self.pending = self.count
+
+    def arrive(self, expect_tx=0):
+        self.tx += expect_tx
+        self.pending -= 1
+        assert self.pending >= 0
+        self._check()
+
+    def complete_tx(self, n):
+        self.tx -= n
+        self._check()
+
+    def try_wait(self, parity):
+        return (self.completed & 1) != parity
+
+
+def simulate_batched_pipeline(n_units, S, n_consumers, seed):
+    """Random interleavings of the batched kernel's producer warp, its
+    consumer warps and the copy engine, following the kernel's waits and
+    arrivals; fails on a read before the bytes land, a stage overwritten
+    while read, a lost or repeated unit, or a wait that can never end."""
+    rng = np.random.default_rng(seed)
+    full = [_MBar(1) for _ in range(S)]
+    empty = [_MBar(n_consumers) for _ in range(S)]
+    info = [None] * S
+    owner = [None] * S
+    landed = set()
+    inflight = []
+    consumed = [[] for _ in range(n_consumers)]
+
+    def producer():
+        i = 0
+        while True:
+            st = i % S
+            if i >= S:
+                par = (i // S - 1) & 1
+                yield lambda st=st, par=par: empty[st].try_wait(par)
+            if i >= n_units:
+                info[st] = -1
+                full[st].arrive()
+                break
+            info[st] = i
+            owner[st] = i
+            full[st].arrive(expect_tx=64)
+            inflight.append((st, i))
+            i += 1
+        for m in range(1, S):
+            if m > i:
+                break
+            j = i - m
+            yield lambda j=j: full[j % S].try_wait((j // S) & 1)
+
+    def consumer(w):
+        i = 0
+        while True:
+            st = i % S
+            yield lambda st=st, par=(i // S) & 1: full[st].try_wait(par)
+            u = info[st]
+            if u == -1:
+                return
+            assert u in landed and owner[st] == u
+            consumed[w].append(u)
+            yield lambda: True  # reading the stage takes time
+            assert owner[st] == u, "stage overwritten while being read"
+            empty[st].arrive()
+            i += 1
+
+    actors = {"p": producer()}
+    actors.update({w: consumer(w) for w in range(n_consumers)})
+    waits = {}
+    for name, g in actors.items():
+        waits[name] = next(g, None)
+    live = {n for n, wt in waits.items() if wt is not None}
+    steps = 0
+    while live or inflight:
+        ready = [n for n in live if waits[n]()]
+        choices = ready + (["copy"] if inflight else [])
+        assert choices, "deadlock: no actor can proceed"
+        c = choices[rng.integers(len(choices))]
+        if c == "copy":
+            st, u = inflight.pop(rng.integers(len(inflight)))
+            landed.add(u)
+            full[st].complete_tx(64)
+        else:
+            nxt = next(actors[c], None)
+            if nxt is None:
+                live.discard(c)
+            else:
+                waits[c] = nxt
+        steps += 1
+        assert steps < 200000
+    for w in range(n_consumers):
+        assert consumed[w] == list(range(n_units))
+
+
+@pytest.mark.parametrize("S", [2, 3, 4])
+def test_batched_pipeline_protocol(S):
+    for n_units in (0, 1, 2, S, S + 1, 7, 23):
+        for seed in range(12):
+            simulate_batched_pipeline(n_units, S, 8, seed * 31 + n_units)
