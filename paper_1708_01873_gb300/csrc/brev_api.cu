@@ -261,6 +261,24 @@ static Choice choose_default(int k, int E, bool inplace, bool vec16) {
   return {false, nullptr};
 }
 
+// Launch with programmatic stream serialisation: the kernel's CTAs may
+// start while the previous kernel in the stream finishes, and wait for it
+// themselves (pdl_wait) before touching global memory.
+cudaError_t launch_pdl(const void* kern, unsigned grid, unsigned threads, void** args,
+                       unsigned smem, cudaStream_t stream) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, kern, args);
+}
+
 static brev_status launch_choice(const Choice& c, void* dst, const void* src, int k, int E,
                                  cudaStream_t stream) {
   cudaError_t e;
@@ -270,7 +288,7 @@ static brev_status launch_choice(const Choice& c, void* dst, const void* src, in
     char* d = (char*)dst;
     const char* s = (const char*)src;
     void* args[] = {(void*)&d, (void*)&s, (void*)&k};
-    e = cudaLaunchKernel(kern, dim3(1), dim3(256), args, smem, stream);
+    e = launch_pdl(kern, 1, 256, args, smem, stream);
     if (e != cudaSuccess) return cuda_error(e, "small-array kernel launch");
     note_launch();
     return BREV_OK;
@@ -284,15 +302,13 @@ static brev_status launch_choice(const Choice& c, void* dst, const void* src, in
     char* d = (char*)dst;
     const char* s = (const char*)src;
     void* args[] = {(void*)&d, (void*)&s, (void*)&k};
-    e = cudaLaunchKernel(t->kernel, dim3((unsigned)grid), dim3(t->threads), args, t->smem,
-                         stream);
+    e = launch_pdl(t->kernel, (unsigned)grid, t->threads, args, t->smem, stream);
   } else {
     const int w = k - 2 * t->bx;
     const unsigned long long grid = (unsigned long long)count_lt(w) + count_self(w);
     char* d = (char*)dst;
     void* args[] = {(void*)&d, (void*)&k};
-    e = cudaLaunchKernel(t->kernel, dim3((unsigned)grid), dim3(t->threads), args, t->smem,
-                         stream);
+    e = launch_pdl(t->kernel, (unsigned)grid, t->threads, args, t->smem, stream);
   }
   if (e != cudaSuccess) return cuda_error(e, "tile kernel launch");
   note_launch();

@@ -33,6 +33,24 @@
 namespace brev {
 
 // ----------------------------------------------------------------- rev --
+// Programmatic dependent launch.  The library's kernels are launched with
+// programmatic stream serialisation, so a kernel's CTAs may start while
+// the previous kernel in the stream is still finishing.  pdl_wait blocks
+// until that grid has completed and its memory is visible; every CTA calls
+// it before its first global-memory access (work on shared memory only,
+// such as a twiddle table, may come before).  pdl_release lets the next
+// kernel in the stream begin launching; its CTAs then wait in their own
+// pdl_wait.  Both are no-ops when the kernel was launched without the
+// attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_enter() {
+  pdl_wait();
+  pdl_release();
+}
+
 // rev_w(v) for 0 <= w <= 32 using the single-instruction 32-bit reversal.
 __device__ __forceinline__ uint32_t rev_bits(uint32_t v, int w) {
   return w == 0 ? 0u : (__brev(v) >> (32 - w));

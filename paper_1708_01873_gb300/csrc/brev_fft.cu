@@ -198,7 +198,9 @@ __global__ void __launch_bounds__(Geom<E, 16, B, B>::THREADS, BREV_FFT_MIN_CTAS)
   using T = typename Cplx<E>::T;
   extern __shared__ uint4 smem_u4[];
   T* tw = reinterpret_cast<T*>(smem_u4 + G::CHUNKS);
-  fill_twiddles<E, B>(tw);
+  pdl_release();
+  fill_twiddles<E, B>(tw);  // shared memory only: overlaps the previous kernel's tail
+  pdl_wait();
   const int wy = k - 2 * B;
   const uint32_t y = blockIdx.x;
   const uint32_t ry = rev_bits(y, wy);
@@ -216,7 +218,9 @@ __global__ void __launch_bounds__(Geom<E, 16, B, B>::THREADS, BREV_FFT_MIN_CTAS)
   using T = typename Cplx<E>::T;
   extern __shared__ uint4 smem_u4[];
   T* tw = reinterpret_cast<T*>(smem_u4 + 2 * G::CHUNKS);
-  fill_twiddles<E, B>(tw);
+  pdl_release();
+  fill_twiddles<E, B>(tw);  // shared memory only: overlaps the previous kernel's tail
+  pdl_wait();
   const int wy = k - 2 * B;
   const uint32_t npairs = count_lt(wy);
   const uint32_t q = blockIdx.x;
@@ -250,6 +254,7 @@ __global__ void __launch_bounds__(256) k_fft_small(char* dst, const char* src, i
   using T = typename Cplx<E>::T;
   extern __shared__ uint4 smem_u4[];
   T* a = reinterpret_cast<T*>(smem_u4);
+  pdl_enter();
   const uint32_t n = 1u << k;
   const T* s = reinterpret_cast<const T*>(src);
   for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) a[rev_bits(i, k)] = s[i];
@@ -353,7 +358,7 @@ extern "C" brev_status brev_fft_stages(void* dst, const void* src, int log2n, in
     const char* sr = (const char*)src;
     int kk = k, SS = S, inv = inverse ? 1 : 0;
     void* args[] = {(void*)&d, (void*)&sr, (void*)&kk, (void*)&SS, (void*)&inv};
-    e = cudaLaunchKernel(kern, dim3(1), dim3(256), args, smem, s);
+    e = launch_pdl(kern, 1, 256, args, smem, s);
     if (e != cudaSuccess) return cuda_error(e, "fused FFT launch");
     note_launch();
     return BREV_OK;
@@ -368,7 +373,7 @@ extern "C" brev_status brev_fft_stages(void* dst, const void* src, int log2n, in
     if (e != cudaSuccess) return cuda_error(e, "shared-memory limit");
     char* d = (char*)dst;
     void* args[] = {(void*)&d, (void*)&kk, (void*)&SS, (void*)&inv};
-    e = cudaLaunchKernel(K.inplace, dim3((unsigned)grid), dim3(K.threads), args, smem, s);
+    e = launch_pdl(K.inplace, (unsigned)grid, K.threads, args, smem, s);
   } else {
     const unsigned long long grid = 1ull << (k - 2 * K.B);
     const unsigned smem = K.tile_bytes + tw_bytes;
@@ -377,7 +382,7 @@ extern "C" brev_status brev_fft_stages(void* dst, const void* src, int log2n, in
     char* d = (char*)dst;
     const char* sr = (const char*)src;
     void* args[] = {(void*)&d, (void*)&sr, (void*)&kk, (void*)&SS, (void*)&inv};
-    e = cudaLaunchKernel(K.oop, dim3((unsigned)grid), dim3(K.threads), args, smem, s);
+    e = launch_pdl(K.oop, (unsigned)grid, K.threads, args, smem, s);
   }
   if (e != cudaSuccess) return cuda_error(e, "fused FFT launch");
   note_launch();

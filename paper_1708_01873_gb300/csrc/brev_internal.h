@@ -49,6 +49,11 @@ brev_status cuda_error(cudaError_t e, const char* what);
 // Raise the dynamic shared-memory limit of `kernel` to `smem` on the
 // current device (once per kernel and device).
 cudaError_t ensure_smem(const void* kernel, unsigned smem);
+// Kernel launch with programmatic stream serialisation, for kernels that
+// call pdl_wait before their first global access (all but the batched
+// kernel, whose launch follows its ticket reset in the stream).
+cudaError_t launch_pdl(const void* kern, unsigned grid, unsigned threads, void** args,
+                       unsigned smem, cudaStream_t stream);
 int current_device_sm_count();
 // Validate a device range (device or managed memory, inside one allocation).
 brev_status check_device_range(const void* p, uint64_t bytes, const char* what);

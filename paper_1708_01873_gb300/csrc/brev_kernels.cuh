@@ -14,6 +14,7 @@ __global__ void __launch_bounds__(Geom<E, W, BX, BZ>::THREADS)
     k_tile_oop(char* __restrict__ dst, const char* __restrict__ src, int k) {
   using G = Geom<E, W, BX, BZ>;
   extern __shared__ uint4 smem_u4[];
+  pdl_enter();
   const int wy = k - BX - BZ;
   const uint32_t y =
       (ORDER == 1 && wy >= BLOCK_ORDER_MIN_W) ? blocked_tile(blockIdx.x, wy) : blockIdx.x;
@@ -27,6 +28,7 @@ __global__ void __launch_bounds__(Geom<E, W, B, B>::THREADS)
     k_tile_inplace(char* data, int k) {
   using G = Geom<E, W, B, B>;
   extern __shared__ uint4 smem_u4[];
+  pdl_enter();
   tile_inplace_body<G, G::THREADS, ORDER>(data, k, blockIdx.x,
                                           reinterpret_cast<typename ChunkT<W>::type*>(smem_u4));
 }
@@ -35,6 +37,7 @@ __global__ void __launch_bounds__(Geom<E, W, B, B>::THREADS)
 template <int E>
 __global__ void __launch_bounds__(256) k_small(char* dst, const char* src, int k) {
   extern __shared__ uint4 smem_u4[];
+  pdl_enter();
   small_body<E>(dst, src, k, blockDim.x, reinterpret_cast<typename ChunkT<E>::type*>(smem_u4));
 }
 

@@ -27,6 +27,7 @@ __global__ void __launch_bounds__(TR_THREADS)
                 int bz) {
   extern __shared__ uint4 smem_u4[];
   auto* sm = reinterpret_cast<typename ChunkT<W>::type*>(smem_u4);
+  pdl_enter();
   const int lc = c - bz;
   const uint64_t t = blockIdx.x;
   const uint64_t tr = t >> lc, tc = t & ((1ull << lc) - 1);
@@ -83,6 +84,7 @@ template <int E, int W>
 __global__ void __launch_bounds__(TR_THREADS) k_transpose_inplace(char* data, int a, int b) {
   extern __shared__ uint4 smem_u4[];
   auto* sm = reinterpret_cast<typename ChunkT<W>::type*>(smem_u4);
+  pdl_enter();
   const uint64_t T = 1ull << (a - b);
   const uint64_t npairs = T * (T - 1) / 2;
   const uint32_t q = blockIdx.x;
@@ -115,6 +117,7 @@ __global__ void __launch_bounds__(TR_THREADS)
     k_segments(char* data, int m, int b, unsigned units) {
   extern __shared__ uint4 smem_u4[];
   auto* sm = reinterpret_cast<typename ChunkT<W>::type*>(smem_u4);
+  pdl_enter();
   if (b == 0) {
     char* seg = data + ((uint64_t)blockIdx.x << m) * E;
     small_body<E>(seg, seg, m, TR_THREADS, reinterpret_cast<typename ChunkT<E>::type*>(sm));
@@ -186,7 +189,7 @@ static brev_status launch(const void* kern, unsigned long long grid, unsigned sm
                           cudaStream_t stream, const char* what) {
   cudaError_t e = ensure_smem(kern, smem);
   if (e != cudaSuccess) return cuda_error(e, "shared-memory limit");
-  e = cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(TR_THREADS), args, smem, stream);
+  e = launch_pdl(kern, (unsigned)grid, TR_THREADS, args, smem, stream);
   if (e != cudaSuccess) return cuda_error(e, what);
   note_launch();
   return BREV_OK;
