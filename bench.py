@@ -582,8 +582,12 @@ def bench_batched(torch, brev, inputs, device, stream, sampler, reduce_max, barr
         ms = reduce_max(ea.elapsed_time(eb)) / reps
         out[name] = {"ms": round(ms, 3), "gbs": round(total / (ms * 1e-3) / 1e9, 1)}
     plan.close()
+    tuned_b = sorted({(E, k, brev.brev_batched_shape(k, E)) for E in (8, 16)
+                      for k in range(8, kmax + 1)})
     res = {"workload": f"{count} arrays, k uniform in [8,{kmax}], E uniform in {{8,16}} "
                        "(seed 4), in place; persistent = one launch per batch",
+           "tile_exponent_b": {f"E{E}_k{k}": b for E, k, b in tuned_b},
+           "tile_exponent_from": "autotuned table (brev_autotune, tune_gb300.json)",
            "bytes_per_batch": total, "launches_in_loop": int(loop_launches), **out,
            "speedup_persistent_graph_vs_loop": round(out["loop"]["ms"] /
                                                      out["persistent_graph"]["ms"], 2),

@@ -288,6 +288,16 @@ BREV_API brev_status brev_permute_host(void *dst_host, const void *src_host, int
 BREV_API brev_status brev_tile_shape(int log2n, int elem_bytes, int in_place, int *bx, int *bz,
                                      int *order);
 
+/* Tile exponent b the batched kernel uses for an array of 2^log2n elements
+ * of elem_bytes (square 2^b x 2^b tiles staged by bulk copies; b = 0 means
+ * the whole array is staged in one unit).  The tuned value when the tuner
+ * or a loaded cache set one for (log2n, elem_bytes), else the built-in
+ * choice.  BREV_ERR_UNSUPPORTED: such an array is not run by the batched
+ * kernel (element sizes 1 and 2, or log2n <= 1, which is the identity);
+ * the batched calls permute it with a single-array launch instead.
+ * Host-only query, no GPU needed. */
+BREV_API brev_status brev_batched_shape(int log2n, int elem_bytes, int *b);
+
 /* Run the permutation with a forced tile shape and launch order (tests and
  * the tuner).  Out-of-place accepts bx != bz; in-place requires bx == bz.
  * Shapes that are not compiled in return BREV_ERR_UNSUPPORTED.  src == dst
@@ -304,8 +314,11 @@ BREV_API brev_status brev_shape_at(int elem_bytes, int in_place, int i, int *bx,
 
 /* Time every compiled shape for k in [k_min, k_max] (out-of-place and
  * in-place), keep the fastest in the library's table, and, if cache_path
- * is not NULL, write the table as JSON.  Allocates and frees its own
- * device buffers; blocks the calling thread. */
+ * is not NULL, write the table as JSON.  For elem_bytes 4, 8 and 16 it also
+ * times the batched kernel's tile exponent b for each k up to 24 on a
+ * batch of equal arrays (up to 4096 arrays, about 256 MiB), and keeps the
+ * fastest (brev_batched_shape).  Allocates and frees its own device
+ * buffers; blocks the calling thread. */
 BREV_API brev_status brev_autotune(int k_min, int k_max, int elem_bytes, const char *cache_path);
 
 /* Load a table written by brev_autotune.  Entries whose device name or SM
@@ -313,7 +326,8 @@ BREV_API brev_status brev_autotune(int k_min, int k_max, int elem_bytes, const c
  * the device-name query. */
 BREV_API brev_status brev_load_tune_cache(const char *cache_path);
 
-/* Forget tuned shapes (back to the built-in defaults). */
+/* Forget tuned shapes and batched tile exponents (back to the built-in
+ * defaults). */
 BREV_API void brev_reset_tuning(void);
 
 /* ---------------------------------------------------------------- info */

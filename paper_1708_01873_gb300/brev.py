@@ -80,6 +80,7 @@ SIGNATURES = {
                                      _i, ctypes.POINTER(ServerRequest), _u64,
                                      ctypes.POINTER(ServerStats)]),
     "brev_tile_shape": (_i, [_i, _i, _i, _ip, _ip, _ip]),
+    "brev_batched_shape": (_i, [_i, _i, _ip]),
     "brev_permute_shape": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _vp]),
     "brev_shape_count": (_i, [_i, _i]),
     "brev_shape_at": (_i, [_i, _i, _i, _ip, _ip, _ip]),
@@ -381,6 +382,15 @@ def brev_tile_shape(log2n: int, elem_bytes: int, in_place: bool) -> tuple[int, i
     _check(lib().brev_tile_shape(log2n, elem_bytes, int(bool(in_place)), ctypes.byref(bx),
                                  ctypes.byref(bz), ctypes.byref(order)), "brev_tile_shape")
     return bx.value, bz.value, order.value
+
+
+def brev_batched_shape(log2n: int, elem_bytes: int) -> int:
+    """Tile exponent b the batched kernel uses for such an array (0 = the
+    whole array staged as one unit); BrevError if it runs as a single-array
+    launch inside a batch."""
+    b = ctypes.c_int()
+    _check(lib().brev_batched_shape(log2n, elem_bytes, ctypes.byref(b)), "brev_batched_shape")
+    return b.value
 
 
 def brev_shapes(elem_bytes: int, in_place: bool) -> list[tuple[int, int, int]]:

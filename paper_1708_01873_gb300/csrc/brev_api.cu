@@ -226,6 +226,15 @@ static int default_b(int E, bool inplace) {
 // tuned (bx, bz, order) per element size, in-place flag and k; bx = 0: not tuned
 static int8_t g_tuned[5][2][BREV_MAX_LOG2N + 1][3];
 static double g_tuned_gbs[5][2][BREV_MAX_LOG2N + 1];
+// tuned batched tile exponent + 1 per element size and k (0: not tuned);
+// read without the lock on every array of a batched call
+static std::atomic<int8_t> g_tuned_batched[5][BREV_MAX_LOG2N + 1];
+static double g_tuned_batched_gbs[5][BREV_MAX_LOG2N + 1];
+
+int tuned_batched_b(int k, int E) {
+  if (k < 0 || k > BREV_MAX_LOG2N || !valid_E(E)) return -1;
+  return (int)g_tuned_batched[e_index(E)][k].load(std::memory_order_relaxed) - 1;
+}
 
 struct Choice {
   bool small;
@@ -546,6 +555,9 @@ void brev_reset_tuning(void) {
   std::lock_guard<std::mutex> lk(g_mu);
   memset(g_tuned, 0, sizeof(g_tuned));
   memset(g_tuned_gbs, 0, sizeof(g_tuned_gbs));
+  for (auto& row : g_tuned_batched)
+    for (auto& v : row) v.store(0, std::memory_order_relaxed);
+  memset(g_tuned_batched_gbs, 0, sizeof(g_tuned_batched_gbs));
 }
 
 static bool device_identity(std::string* name, int* sms) {
@@ -581,6 +593,14 @@ static brev_status write_cache(const char* path) {
                 first ? "" : ",", Es[ei], k, ip, t[0], t[1], t[2], g_tuned_gbs[ei][ip][k]);
         first = false;
       }
+  for (int ei = 0; ei < 5; ++ei)
+    for (int k = 0; k <= BREV_MAX_LOG2N; ++k) {
+      const int v = g_tuned_batched[ei][k].load(std::memory_order_relaxed);
+      if (v <= 0) continue;
+      fprintf(f, "%s\n  {\"elem_bytes\": %d, \"log2n\": %d, \"batched_b\": %d, \"gbs\": %.1f}",
+              first ? "" : ",", Es[ei], k, v - 1, g_tuned_batched_gbs[ei][k]);
+      first = false;
+    }
   fprintf(f, "\n]}\n");
   fclose(f);
   return BREV_OK;
@@ -638,7 +658,20 @@ brev_status brev_load_tune_cache(const char* path) {
   for (const char* p = strchr(ent, '{'); p; p = strchr(p, '{')) {
     const char* q = strchr(p, '}');
     if (!q) break;
-    long E = 0, k = -1, ip = -1, bx = 0, bz = 0, order = 0;
+    long E = 0, k = -1, ip = -1, bx = 0, bz = 0, order = 0, bb = -1;
+    if (json_int(p, q, "batched_b", &bb)) {  // batched tile exponent
+      if (json_int(p, q, "elem_bytes", &E) && json_int(p, q, "log2n", &k) && valid_E((int)E) &&
+          k >= 0 && k <= BREV_MAX_LOG2N && bb >= 0 && bb <= 7) {
+        int cand[8], def = -1;
+        const int nc = batched_candidates((int)k, (int)E, cand, &def);
+        if (std::find(cand, cand + nc, (int)bb) != cand + nc) {
+          g_tuned_batched[e_index((int)E)][k].store((int8_t)(bb + 1), std::memory_order_relaxed);
+          ++loaded;
+        }
+      }
+      p = q + 1;
+      continue;
+    }
     if (!json_int(p, q, "order", &order)) order = 0;  // tables written before orders existed
     if (json_int(p, q, "elem_bytes", &E) && json_int(p, q, "log2n", &k) &&
         json_int(p, q, "in_place", &ip) && json_int(p, q, "bx", &bx) &&
@@ -655,6 +688,73 @@ brev_status brev_load_tune_cache(const char* path) {
     p = q + 1;
   }
   return BREV_OK;
+}
+
+// Batched tile exponent per k: time every candidate b on a batch of equal
+// arrays of 2^k elements (up to 4096 of them, about 256 MiB in all),
+// L2 flushed before each launch, and keep the fastest unless the built-in
+// choice is within 3 %.
+static brev_status autotune_batched(int k_min, int k_max, int E, cudaStream_t st, void* fl,
+                                    size_t flush_bytes, cudaEvent_t e0, cudaEvent_t e1) {
+  constexpr uint64_t BUDGET = 256ull << 20;
+  constexpr int MAX_ARRAYS = 4096;
+  void* buf = nullptr;
+  cudaError_t e = cudaMalloc(&buf, BUDGET);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(BREV_ERR_OOM, "batched autotune buffer: %s", cudaGetErrorString(e));
+  }
+  cudaMemsetAsync(buf, 0x3C, BUDGET, st);
+  brev_status result = BREV_OK;
+  std::vector<BatchItem> items;
+  for (int k = std::max(k_min, 2); k <= k_max && result == BREV_OK; ++k) {
+    int cand[8], def = -1;
+    const int nc = batched_candidates(k, E, cand, &def);
+    if (nc < 2 || def < 0) continue;  // nothing to choose
+    const uint64_t bytes = (uint64_t)E << k;
+    const int count = (int)std::min<uint64_t>(MAX_ARRAYS, BUDGET / bytes);
+    if (count < 1) continue;
+    items.assign(count, BatchItem{});
+    for (int i = 0; i < count; ++i) items[i] = BatchItem{(char*)buf + (uint64_t)i * bytes, k, E};
+    double best = 1e30, def_med = 0;
+    int best_b = -1;
+    for (int c = 0; c < nc && result == BREV_OK; ++c) {
+      std::vector<float> ms;
+      for (int r = 0; r < 9 && result == BREV_OK; ++r) {
+        cudaMemsetAsync(fl, r & 0xFF, flush_bytes, st);
+        cudaEventRecord(e0, st);
+        result = batched_launch_forced(items.data(), count, cand[c], st);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+          result = cuda_error(cudaGetLastError(), "batched autotune timing");
+          break;
+        }
+        float m = 0;
+        cudaEventElapsedTime(&m, e0, e1);
+        if (r >= 2) ms.push_back(m);  // two warm-up runs
+      }
+      if (result != BREV_OK) break;
+      std::sort(ms.begin(), ms.end());
+      const double med = ms[ms.size() / 2];
+      if (cand[c] == def) def_med = med;
+      if (med < best) {
+        best = med;
+        best_b = cand[c];
+      }
+    }
+    if (result != BREV_OK) break;
+    if (def_med > 0 && best > 0.97 * def_med) {
+      best = def_med;
+      best_b = def;
+    }
+    if (best_b >= 0) {
+      g_tuned_batched[e_index(E)][k].store((int8_t)(best_b + 1), std::memory_order_relaxed);
+      g_tuned_batched_gbs[e_index(E)][k] = 2.0 * (double)bytes * count / (best * 1e-3) / 1e9;
+    }
+  }
+  cudaStreamSynchronize(st);
+  cudaFree(buf);
+  return result;
 }
 
 brev_status brev_autotune(int k_min, int k_max, int elem_bytes, const char* cache_path) {
@@ -742,6 +842,8 @@ brev_status brev_autotune(int k_min, int k_max, int elem_bytes, const char* cach
       }
     }
   }
+  if (result == BREV_OK && (E == 4 || E == 8 || E == 16))
+    result = autotune_batched(k_min, std::min(k_max, 24), E, st, fl, flush_bytes, e0, e1);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   cudaStreamSynchronize(st);

@@ -328,17 +328,46 @@ static bool batched_shape_ok(int E, int b) {
   return false;
 }
 
-// Tile exponent for an in-place array in the batched kernel.  Every body
-// runs with 256 threads, so the tile should give each thread several
-// 16-byte chunks: 16 KiB tiles with 256-512-byte rows (E=16: b=5, E=8:
-// b=5, E=4: b=6), smaller only when the array is too short for them; 0
-// stages the whole array in one CTA (k < 2 b_min).
-static int batched_b(int k, int E) {
+// Built-in tile exponent for an in-place array in the batched kernel.
+// 256 consumer threads should each get several 16-byte chunks per tile:
+// 16 KiB tiles with 256-512-byte rows (E=16: b=5, E=8: b=5, E=4: b=6),
+// smaller only when the array is too short for them; 0 stages the whole
+// array as one unit (k < 2 b_min).
+static int batched_b_default(int k, int E) {
   const int bmin = b_min_for(E);
   if (k < 2 * bmin) return 0;
   const int pref = E == 16 ? 5 : (E == 8 ? 5 : 6);
   const int b = std::min(pref, k / 2);
   return batched_shape_ok(E, b) ? b : -1;
+}
+
+// Largest array staged whole (b = 0) at or above 2 b_min: no larger than
+// the largest tile-pair stage, so it never raises the kernel's stage size.
+constexpr unsigned long long BATCH_WHOLE_MAX_BYTES = 32768;
+
+static bool batched_b_valid(int k, int E, int b) {
+  if (!(E == 4 || E == 8 || E == 16) || k <= 1) return false;
+  const int bmin = b_min_for(E);
+  if (b == 0) return k < 2 * bmin || ((unsigned long long)E << k) <= BATCH_WHOLE_MAX_BYTES;
+  return k >= 2 * bmin && b >= bmin && 2 * b <= k && batched_shape_ok(E, b);
+}
+
+int batched_candidates(int k, int E, int* out, int* def) {
+  int n = 0;
+  *def = -1;
+  if (!(E == 4 || E == 8 || E == 16) || k <= 1) return 0;
+  for (int b = 0; b <= 6; ++b)
+    if (batched_b_valid(k, E, b)) out[n++] = b;
+  *def = batched_b_default(k, E);
+  return n;
+}
+
+// Tile exponent of an array in the batched kernel: the tuned one when
+// present and valid, else the built-in one; -1 = single-array fallback.
+static int batched_b(int k, int E) {
+  const int t = tuned_batched_b(k, E);
+  if (t >= 0 && batched_b_valid(k, E, t)) return t;
+  return batched_b_default(k, E);
 }
 
 struct BatchPlanData {
@@ -348,7 +377,10 @@ struct BatchPlanData {
   std::vector<BatchItem> fallback;  // arrays run with single-array launches
 };
 
-static brev_status build_batch(const BatchItem* items, int count, BatchPlanData* out) {
+// Descriptors and tickets of a batch; force_b >= 0 imposes that tile
+// exponent on every array (which must accept it).
+static brev_status build_batch(const BatchItem* items, int count, BatchPlanData* out,
+                               int force_b = -1) {
   struct Tmp {
     BatchDesc d;
     unsigned long long bytes;
@@ -359,7 +391,13 @@ static brev_status build_batch(const BatchItem* items, int count, BatchPlanData*
     const BatchItem& it = items[i];
     if (it.k <= 1) continue;  // identity
     const bool vec = ((uintptr_t)it.ptr % 16) == 0;
-    const int b = (it.E == 4 || it.E == 8 || it.E == 16) && vec ? batched_b(it.k, it.E) : -1;
+    int b = (it.E == 4 || it.E == 8 || it.E == 16) && vec ? batched_b(it.k, it.E) : -1;
+    if (force_b >= 0) {
+      if (!vec || !batched_b_valid(it.k, it.E, force_b))
+        return set_error(BREV_ERR_UNSUPPORTED, "array %d (k=%d, E=%d) cannot take b=%d", i,
+                         it.k, it.E, force_b);
+      b = force_b;
+    }
     if (b < 0) {
       out->fallback.push_back(it);
       continue;
@@ -450,8 +488,13 @@ static brev_status enqueue_batch(const BatchPlanData& p, const BatchDesc* d_desc
 }
 
 brev_status batched_launch(const BatchItem* items, int count, cudaStream_t stream) {
+  return batched_launch_forced(items, count, -1, stream);
+}
+
+brev_status batched_launch_forced(const BatchItem* items, int count, int b,
+                                  cudaStream_t stream) {
   BatchPlanData p;
-  brev_status s = build_batch(items, count, &p);
+  brev_status s = build_batch(items, count, &p, b);
   if (s != BREV_OK) return s;
   if (p.desc.empty()) return enqueue_batch(p, nullptr, nullptr, stream);
   // stream-ordered workspace: descriptors + ticket counter
@@ -559,6 +602,21 @@ extern "C" brev_status brev_plan_create(void* const* ptr_array, const int* log2n
     return cuda_error(e, "graph instantiate");
   }
   *out_plan = p;
+  return BREV_OK;
+}
+
+extern "C" brev_status brev_batched_shape(int log2n, int elem_bytes, int* b) {
+  if (!b) return set_error(BREV_ERR_INVALID_ARG, "b is NULL");
+  if (log2n < 0 || log2n > BREV_MAX_LOG2N)
+    return set_error(BREV_ERR_INVALID_ARG, "log2n=%d", log2n);
+  const int v = (elem_bytes == 4 || elem_bytes == 8 || elem_bytes == 16) && log2n > 1
+                    ? batched_b(log2n, elem_bytes)
+                    : -1;
+  if (v < 0)
+    return set_error(BREV_ERR_UNSUPPORTED,
+                     "log2n=%d elem_bytes=%d runs as a single-array launch in a batch", log2n,
+                     elem_bytes);
+  *b = v;
   return BREV_OK;
 }
 

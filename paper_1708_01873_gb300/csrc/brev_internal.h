@@ -65,6 +65,16 @@ struct BatchItem {
   int E;
 };
 brev_status batched_launch(const BatchItem* items, int count, cudaStream_t stream);
+// The same launch with tile exponent `b` forced for every array (the
+// tuner's candidates; each array must accept b, see batched_candidates).
+brev_status batched_launch_forced(const BatchItem* items, int count, int b,
+                                  cudaStream_t stream);
+// Tile exponents the batched kernel can use for an array (k, E), into
+// out[0..return); the built-in choice in *def.  0 candidates: the array is
+// not run by the batched kernel.
+int batched_candidates(int k, int E, int* out, int* def);
+// Tuned batched tile exponent for (k, E), or -1 (brev_api.cu).
+int tuned_batched_b(int k, int E);
 // Argument checks of a batch (sizes, alignment, device ranges, no overlap).
 brev_status validate_batch_items(const BatchItem* items, int count);
 // Launch one permutation without argument checks (src == dst: in-place).

@@ -4,7 +4,9 @@
 
 For every element size and k, brev_autotune times each compiled 16-byte
 tile shape out-of-place and in-place (L2 flushed between repetitions,
-median of several runs) and keeps the fastest.  The library loads the
+median of several runs) and keeps the fastest; for 4-, 8- and 16-byte
+elements it also times the batched kernel's tile exponent b per k on a
+batch of equal arrays.  The library loads the
 cache at import when the device name and SM count match (or the file named
 by BREV_TUNE_CACHE).
 """

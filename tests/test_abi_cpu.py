@@ -115,10 +115,57 @@ def test_tune_cache_round_trip_host_only(brev_lib, tmp_path):
         brev_lib.brev_load_tune_cache(str(tmp_path / "missing.json"))
 
 
+def test_batched_shape_choice(brev_lib):
+    """Built-in batched tile exponents: 16 KiB tiles with 256-512-byte rows
+    at large k, smaller tiles for short arrays, whole-array staging below
+    2 b_min, single-array launches for 1- and 2-byte elements."""
+    brev_lib.brev_reset_tuning()
+    b_min = {16: 3, 8: 4, 4: 5}
+    pref = {16: 5, 8: 5, 4: 6}
+    for E in (16, 8, 4):
+        for k in range(2, 35):
+            b = brev_lib.brev_batched_shape(k, E)
+            if k < 2 * b_min[E]:
+                assert b == 0
+            else:
+                assert b == min(pref[E], k // 2) and b >= b_min[E]
+    for E, k in ((16, 0), (16, 1), (2, 20), (1, 20)):
+        with pytest.raises(brev_lib.BrevError):
+            brev_lib.brev_batched_shape(k, E)
+
+
+def test_batched_tune_cache_round_trip_host_only(brev_lib, tmp_path):
+    p = tmp_path / "b.json"
+    entries = [
+        {"elem_bytes": 16, "log2n": 14, "batched_b": 4, "gbs": 1.0},
+        {"elem_bytes": 8, "log2n": 11, "batched_b": 0, "gbs": 1.0},    # 16 KiB staged whole
+        # invalid: b too large for k, shape not in the batched kernel, whole
+        # array too large to stage
+        {"elem_bytes": 16, "log2n": 7, "batched_b": 4, "gbs": 1.0},
+        {"elem_bytes": 4, "log2n": 20, "batched_b": 4, "gbs": 1.0},
+        {"elem_bytes": 16, "log2n": 20, "batched_b": 0, "gbs": 1.0},
+    ]
+    p.write_text(json.dumps({"format": "brev-tune-1", "device": "any", "sm_count": 1,
+                             "entries": entries}))
+    brev_lib.brev_reset_tuning()
+    d = {(k, E): brev_lib.brev_batched_shape(k, E) for k, E in ((7, 16), (20, 4), (20, 16))}
+    brev_lib.brev_load_tune_cache(str(p))
+    assert brev_lib.brev_batched_shape(14, 16) == 4
+    assert brev_lib.brev_batched_shape(11, 8) == 0
+    for (k, E), b in d.items():
+        assert brev_lib.brev_batched_shape(k, E) == b
+    brev_lib.brev_reset_tuning()
+    assert brev_lib.brev_batched_shape(14, 16) == 5
+
+
 def test_shipped_tune_cache_is_valid(brev_lib):
     d = json.load(open(brev_lib.DEFAULT_TUNE_CACHE))
     assert d["format"] == "brev-tune-1" and d["sm_count"] > 0
     for e in d["entries"]:
+        if "batched_b" in e:
+            b = e["batched_b"]
+            assert b == 0 or (2 * b <= e["log2n"] and e["elem_bytes"] in (4, 8, 16))
+            continue
         assert (e["bx"], e["bz"], e.get("order", 0)) in \
             brev_lib.brev_shapes(e["elem_bytes"], bool(e["in_place"]))
         assert e["bx"] + e["bz"] <= e["log2n"]

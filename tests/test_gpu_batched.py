@@ -189,15 +189,29 @@ def test_autotune_and_cache(brev_lib, oracle_lib, cuda_device, tmp_path):
     import json
     d = json.load(open(path))
     assert d["sm_count"] > 0 and d["entries"]
-    for e in d["entries"]:
+    single = [e for e in d["entries"] if "batched_b" not in e]
+    batched = [e for e in d["entries"] if "batched_b" in e]
+    assert single and batched
+    for e in single:
         assert (e["bx"], e["bz"], e["order"]) in \
             brev_lib.brev_shapes(e["elem_bytes"], e["in_place"])
+    # one batched entry per k with a choice (k = 12..16, E = 8)
+    assert sorted(e["log2n"] for e in batched) == list(range(12, 17))
     brev_lib.brev_reset_tuning()
     brev_lib.brev_load_tune_cache(path)
-    for e in d["entries"]:
+    for e in single:
         if e["elem_bytes"] == 8 and 12 <= e["log2n"] <= 16:
             assert brev_lib.brev_tile_shape(e["log2n"], 8, bool(e["in_place"])) == \
                 (e["bx"], e["bz"], e["order"])
+    for e in batched:
+        assert brev_lib.brev_batched_shape(e["log2n"], 8) == e["batched_b"]
+    # a batch under the tuned exponents gives the oracle's result
+    rng = np.random.default_rng(17)
+    arrays, hosts = _make_batch(rng, 40, list(range(12, 17)), [8], 1700)
+    brev_lib.brev_permute_batched(arrays)
+    torch.cuda.synchronize()
+    for a, ex, (k, E, _) in zip(arrays, _expect(oracle_lib, hosts), hosts):
+        assert_bytes_equal(to_bytes(a), ex, E, f"tuned batched k={k}")
     # tuned shapes give the same result
     for k in (12, 16):
         src = device_array(90 + k, k, 8)
