@@ -59,6 +59,7 @@ def parse_args():
     ap.add_argument("--batch-kmax", type=int, default=20)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-next", action="store_true")
+    ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--points-out", default=None,
                     help="write per-point median times of the sweep to this JSON file")
     ap.add_argument("--next-k", type=int, default=28,
@@ -342,6 +343,12 @@ def run_brev(args):
         batched = bench_batched(torch, brev, inputs, device, stream, sampler, reduce_max,
                                 barrier, count=args.batch_count, kmax=args.batch_kmax)
 
+    # ------------------------------------- large single arrays (cfg 3)
+    large_cfg = None
+    if not args.no_large:
+        large_cfg = bench_large(torch, brev, inputs, device, stream, sampler, reduce_max,
+                                barrier, peak, info["nominal_gbs"])
+
     # -------------------------------------------- widened rows (NEXT)
     next_rows = None
     if not args.no_next:
@@ -410,6 +417,7 @@ def run_brev(args):
             "large_arrays_from": "warm-up steps with CUDA events around every launch",
             "batched": batched,
             "serving": serving,
+            "large_single_arrays": large_cfg,
             "transpositions_and_recursive": next_rows,
             "e2e": e2e,
             "gpu_launches": int(launches),
@@ -452,14 +460,10 @@ def load_traffic(kernel_name, k, E, mode):
     return None
 
 
-def bench_next(torch, brev, inputs, device, stream, sampler, reduce_max, barrier, peak,
-               reps=5, warm=2, k=28):
-    """The widened rows: transpositions (square and narrow: the even-odd step
-    and the perfect shuffle) and the paper's recursive method (three passes)
-    against the one-pass tile kernel, all on 4 GiB arrays."""
-    L = brev.lib()
-    sh = stream.cuda_stream
-
+def event_timer(torch, stream, sampler, reduce_max, barrier, reps, warm):
+    """timed(fn): `warm` untimed calls, then the mean of `reps` calls on
+    `stream` between two CUDA events (barrier on both sides, max over
+    ranks); the clock sampler's window covers the timed calls."""
     def timed(fn):
         for _ in range(warm):
             fn()
@@ -474,6 +478,42 @@ def bench_next(torch, brev, inputs, device, stream, sampler, reduce_max, barrier
         barrier()
         sampler.window(w0, time.time())
         return reduce_max(ea.elapsed_time(eb)) / reps
+    return timed
+
+
+def bench_large(torch, brev, inputs, device, stream, sampler, reduce_max, barrier, peak,
+                nominal, reps=5, warm=2):
+    """The large single arrays: k = 30 float32 in place (4 GiB), k = 28
+    complex<double> in place (4 GiB), k = 29 complex<float> out of place
+    (odd k, 4 GiB -> 4 GiB).  Arrays far larger than L2, so no flush."""
+    L = brev.lib()
+    sh = stream.cuda_stream
+    timed = event_timer(torch, stream, sampler, reduce_max, barrier, reps, warm)
+    out = {}
+    for kind, E, k, inplace in (("f32", 4, 30, True), ("c128", 16, 28, True),
+                                ("c64", 8, 29, False)):
+        src = torch.empty((1 << k) * E, dtype=torch.uint8, device=device)
+        inputs.fill_torch(src, 30 + k, kind, chunk=1 << 26)
+        dst = src if inplace else torch.empty_like(src)
+        ms = timed(lambda: L.brev_permute_to(dst.data_ptr(), src.data_ptr(), k, E, sh))
+        gbs = 2 * src.numel() / (ms * 1e-3) / 1e9
+        bx, bz, order = brev.brev_tile_shape(k, E, inplace)
+        out[f"{kind}_k{k}_{'in_place' if inplace else 'out_of_place'}"] = {
+            "ms": round(ms, 4), "gbs": round(gbs, 1), "frac": round(gbs / peak, 4),
+            "frac_nominal": round(gbs / nominal, 4), "tile": [bx, bz, order]}
+        del src, dst
+    torch.cuda.empty_cache()
+    return out
+
+
+def bench_next(torch, brev, inputs, device, stream, sampler, reduce_max, barrier, peak,
+               reps=5, warm=2, k=28):
+    """The widened rows: transpositions (square and narrow: the even-odd step
+    and the perfect shuffle) and the paper's recursive method (three passes)
+    against the one-pass tile kernel, all on 4 GiB arrays."""
+    L = brev.lib()
+    sh = stream.cuda_stream
+    timed = event_timer(torch, stream, sampler, reduce_max, barrier, reps, warm)
 
     out = {}
     E = 16

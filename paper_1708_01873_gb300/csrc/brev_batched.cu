@@ -20,6 +20,7 @@
 #include "brev_async.cuh"
 #include "brev_device.cuh"
 #include "brev_internal.h"
+#include "brev_transpose_units.cuh"
 
 namespace brev {
 
@@ -28,11 +29,19 @@ struct BatchDesc {
   unsigned long long first_ticket;  // tickets [first_ticket, first_ticket + tickets)
   unsigned units;                   // work units of this array
   unsigned grain;                   // units per ticket
-  int k;
+  int k;                            // BATCH_BITREV: log2 n; BATCH_TRANSPOSE: log2 of the side
   int E;
   int b;                            // square tile exponent; 0 = whole array in one CTA
-  int pad_;
+  int mode;                         // BATCH_BITREV or BATCH_TRANSPOSE
 };
+// Descriptor modes: in-place bit reversal of 2^k elements (units: tile
+// pairs (y, rev y) then self-paired tiles), or in-place transposition of a
+// 2^k x 2^k matrix (units: tile pairs (tr, tc), tr < tc, and diagonal
+// tiles, in blocked order).  Both stage one tile or a pair of tiles per
+// unit; they differ only in which tiles and in the row and column maps
+// (reversal vs identity).
+constexpr int BATCH_BITREV = 0;
+constexpr int BATCH_TRANSPOSE = 1;
 
 constexpr int BATCH_THREADS = 256;
 #ifndef BREV_BATCHED_TICKET_BYTES
@@ -93,10 +102,11 @@ constexpr int BATCH_STAGES = BREV_BATCHED_STAGES;
 // Unit staged in one pipeline stage.  nt: 2 = tile pair, 1 = self-paired
 // tile, 0 = small array staged whole, -1 = no unit.
 struct StageInfo {
-  char* a;                    // tile y (the whole array when nt = 0)
-  char* r;                    // tile rev(y)
+  char* a;                    // tile y, or (tr, tc) (the whole array when nt = 0)
+  char* r;                    // its partner tile rev(y), or (tc, tr)
   unsigned long long stride;  // tile row stride in bytes
   int E, b, k, nt;
+  int rev;                    // 1: bit-reversed row and column maps, 0: identity
 };
 
 __host__ __device__ constexpr unsigned padded_row_bytes(int E, int b) {
@@ -125,6 +135,7 @@ __device__ __forceinline__ void issue_unit(const BatchDesc& d, unsigned u, Stage
   s.E = d.E;
   s.b = d.b;
   s.k = d.k;
+  s.rev = d.mode == BATCH_BITREV;
   if (d.b == 0) {
     const uint32_t bytes = (uint32_t)d.E << d.k;
     s.a = s.r = d.ptr;
@@ -137,24 +148,43 @@ __device__ __forceinline__ void issue_unit(const BatchDesc& d, unsigned u, Stage
     }
     return;
   }
-  const int b = d.b, wy = d.k - 2 * b;
-  const uint32_t npairs = count_lt(wy);
-  uint32_t y, ry;
-  if (u < npairs) {
-    y = unrank_lt(u, wy);
-    ry = rev_bits(y, wy);
-    s.nt = 2;
-  } else {
-    y = unrank_self(u - npairs, wy);
-    ry = y;
-    s.nt = 1;
+  const int b = d.b;
+  if (d.mode == BATCH_BITREV) {
+    const int wy = d.k - 2 * b;
+    const uint32_t npairs = count_lt(wy);
+    uint32_t y, ry;
+    if (u < npairs) {
+      y = unrank_lt(u, wy);
+      ry = rev_bits(y, wy);
+      s.nt = 2;
+    } else {
+      y = unrank_self(u - npairs, wy);
+      ry = y;
+      s.nt = 1;
+    }
+    s.stride = (unsigned long long)d.E << (d.k - b);
+    s.a = d.ptr + ((uint64_t)y << b) * d.E;
+    s.r = d.ptr + ((uint64_t)ry << b) * d.E;
+  } else {  // transposition of a 2^k x 2^k matrix
+    const uint32_t T = 1u << (d.k - b);
+    const uint32_t npairs = T * (T - 1) / 2;
+    uint32_t tr, tc;
+    if (T >= 8) {
+      s.nt = blocked_upper(u, T, tr, tc);
+    } else if (u < npairs) {
+      unrank_upper(u, tr, tc);
+      s.nt = 2;
+    } else {
+      tr = tc = u - npairs;
+      s.nt = 1;
+    }
+    s.stride = (unsigned long long)d.E << d.k;
+    s.a = d.ptr + (((uint64_t)tr << (b + d.k)) + ((uint64_t)tc << b)) * d.E;
+    s.r = d.ptr + (((uint64_t)tc << (b + d.k)) + ((uint64_t)tr << b)) * d.E;
   }
   const uint32_t rowb = (uint32_t)d.E << b;
   const uint32_t pitch = padded_row_bytes(d.E, b);
   const int rows = 1 << b;
-  s.stride = (unsigned long long)d.E << (d.k - b);
-  s.a = d.ptr + ((uint64_t)y << b) * d.E;
-  s.r = d.ptr + ((uint64_t)ry << b) * d.E;
   if (lane == 0) {
     *info = s;
     mbar_arrive_expect_tx(full, (uint32_t)s.nt * rows * rowb);
@@ -162,16 +192,19 @@ __device__ __forceinline__ void issue_unit(const BatchDesc& d, unsigned u, Stage
   __syncwarp();
   for (int q = lane; q < s.nt * rows; q += 32) {
     const int t = q >> b, x = q & (rows - 1);
-    bulk_g2s(buf + (uint32_t)t * rows * pitch + rev_bits((uint32_t)x, b) * pitch,
+    const uint32_t X = s.rev ? rev_bits((uint32_t)x, b) : (uint32_t)x;
+    bulk_g2s(buf + (uint32_t)t * rows * pitch + X * pitch,
              (t ? s.r : s.a) + (uint64_t)x * s.stride, rowb, full);
   }
 }
 
-// Store one staged 2^b x 2^b tile (rows at pitch P, row X = rev(x)) into
-// the destination tile: output row rev(z), column X.
+// Store one staged 2^b x 2^b tile (rows at pitch P, row X = rev(x), or x
+// when rev = 0) into the destination tile: output row rev(z) (or z),
+// column X.
 template <int E>
 __device__ __forceinline__ void store_staged_tile(const unsigned char* sm, char* dst,
-                                                  uint64_t stride, int b, uint32_t pitch) {
+                                                  uint64_t stride, int b, uint32_t pitch,
+                                                  int rev) {
   constexpr int V = 16 / E;
   constexpr int LOG_V = ilog2c(V);
   const int log_c = b - LOG_V;
@@ -190,7 +223,8 @@ __device__ __forceinline__ void store_staged_tile(const unsigned char* sm, char*
     xpose<E, 16>(blk, out);
 #pragma unroll
     for (int e = 0; e < V; ++e) {
-      const uint32_t Z = rev_bits((uint32_t)(c * V + e), b);
+      const uint32_t z = (uint32_t)(c * V + e);
+      const uint32_t Z = rev ? rev_bits(z, b) : z;
       gstore<16>(dst + (uint64_t)Z * stride + (unsigned)d * 16, out[e]);
     }
   }
@@ -199,7 +233,7 @@ __device__ __forceinline__ void store_staged_tile(const unsigned char* sm, char*
 template <int E>
 __device__ BREV_BATCHED_BODY_ATTR void store_staged_unit(const unsigned char* sm, char* a,
                                                         char* r, uint64_t stride, int b, int k,
-                                                        int nt) {
+                                                        int nt, int rev) {
   using C = typename ChunkT<E>::type;
   if (nt == 0) {  // small array: out[j] = in[rev j], coalesced writes
     const uint32_t n = 1u << k;
@@ -209,8 +243,8 @@ __device__ BREV_BATCHED_BODY_ATTR void store_staged_unit(const unsigned char* sm
     return;
   }
   const uint32_t pitch = padded_row_bytes(E, b);
-  store_staged_tile<E>(sm, r, stride, b, pitch);  // tile y's data into tile rev(y)
-  if (nt == 2) store_staged_tile<E>(sm + ((uint32_t)pitch << b), a, stride, b, pitch);
+  store_staged_tile<E>(sm, r, stride, b, pitch, rev);  // tile a's data into tile r
+  if (nt == 2) store_staged_tile<E>(sm + ((uint32_t)pitch << b), a, stride, b, pitch, rev);
 }
 
 // Warps 0..7 store (consumers, threads 0..255); warp 8 is the producer.
@@ -222,9 +256,12 @@ __device__ BREV_BATCHED_BODY_ATTR void store_staged_unit(const unsigned char* sm
 constexpr int BATCH_CONSUMER_WARPS = BATCH_THREADS / 32;
 constexpr int BATCH_BLOCK = BATCH_THREADS + 32;
 
+// count > 0: descriptors desc[0..count) in global memory; count = 0: the
+// single descriptor `one`, passed by value.
 __global__ void __launch_bounds__(BATCH_BLOCK, BREV_BATCHED_MIN_CTAS)
-    k_batched(const BatchDesc* __restrict__ desc, int count, unsigned long long tickets,
-              unsigned long long* ticket_ctr, unsigned stage_bytes) {
+    k_batched(const BatchDesc* __restrict__ desc, int count, const BatchDesc one,
+              unsigned long long tickets, unsigned long long* ticket_ctr,
+              unsigned stage_bytes) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[BATCH_STAGES], empty[BATCH_STAGES];
   __shared__ StageInfo info[BATCH_STAGES];
@@ -265,8 +302,13 @@ __global__ void __launch_bounds__(BATCH_BLOCK, BREV_BATCHED_MIN_CTAS)
         if (t >= tickets) {
           more = false;
         } else {
-          a = find_array(desc, count, t);
-          d = desc[a];
+          if (count > 0) {
+            a = find_array(desc, count, t);
+            d = desc[a];
+          } else {
+            a = 0;
+            d = one;
+          }
           u = (unsigned)(t - d.first_ticket) * d.grain;
           ulast = min(u + d.grain, d.units);
           if (lane == 0) pending = atomicAdd(ticket_ctr, 1ull);
@@ -306,9 +348,9 @@ __global__ void __launch_bounds__(BATCH_BLOCK, BREV_BATCHED_MIN_CTAS)
     if (s.nt < 0) return;
     const unsigned char* buf = smem + (size_t)st * stage_bytes;
     switch (s.E) {
-      case 16: store_staged_unit<16>(buf, s.a, s.r, s.stride, s.b, s.k, s.nt); break;
-      case 8: store_staged_unit<8>(buf, s.a, s.r, s.stride, s.b, s.k, s.nt); break;
-      case 4: store_staged_unit<4>(buf, s.a, s.r, s.stride, s.b, s.k, s.nt); break;
+      case 16: store_staged_unit<16>(buf, s.a, s.r, s.stride, s.b, s.k, s.nt, s.rev); break;
+      case 8: store_staged_unit<8>(buf, s.a, s.r, s.stride, s.b, s.k, s.nt, s.rev); break;
+      case 4: store_staged_unit<4>(buf, s.a, s.r, s.stride, s.b, s.k, s.nt, s.rev); break;
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[st]);
@@ -454,14 +496,16 @@ static int batched_grid(unsigned smem) {
 static brev_status launch_batched_kernel(const BatchDesc* d_desc, int count,
                                          unsigned long long tickets,
                                          unsigned long long* d_ticket, unsigned stage_bytes,
-                                         cudaStream_t stream) {
+                                         cudaStream_t stream, const BatchDesc* one = nullptr) {
+  BatchDesc one_v{};
+  if (one) one_v = *one;
   const unsigned smem = BATCH_STAGES * stage_bytes;
   cudaError_t e = ensure_smem((const void*)k_batched, smem);
   if (e != cudaSuccess) return cuda_error(e, "shared-memory limit of the batched kernel");
   const int grid =
       (int)std::min<unsigned long long>((unsigned long long)batched_grid(smem), tickets);
-  void* args[] = {(void*)&d_desc, (void*)&count, (void*)&tickets, (void*)&d_ticket,
-                  (void*)&stage_bytes};
+  void* args[] = {(void*)&d_desc, (void*)&count, (void*)&one_v, (void*)&tickets,
+                  (void*)&d_ticket, (void*)&stage_bytes};
   e = cudaLaunchKernel((const void*)k_batched, dim3(grid), dim3(BATCH_BLOCK), args, smem,
                        stream);
   if (e != cudaSuccess) return cuda_error(e, "batched kernel launch");
@@ -516,6 +560,55 @@ brev_status batched_launch_forced(const BatchItem* items, int count, int b,
   s = enqueue_batch(p, (const BatchDesc*)ws, d_ticket, stream);
   cudaFreeAsync(ws, stream);
   return s;
+}
+
+int transpose_pipelined_b(int E) {
+  switch (E) {
+    case 16: return 5;
+    case 8: return 5;
+    case 4: return 6;
+  }
+  return -1;
+}
+
+brev_status transpose_inplace_pipelined(void* data, int a, int E, cudaStream_t stream) {
+  const int b = transpose_pipelined_b(E);
+  if (b < 0 || a < b || ((uintptr_t)data % 16) != 0)
+    return set_error(BREV_ERR_UNSUPPORTED, "pipelined transposition: a=%d E=%d", a, E);
+  BatchDesc d{};
+  d.ptr = (char*)data;
+  d.k = a;
+  d.E = E;
+  d.b = b;
+  d.mode = BATCH_TRANSPOSE;
+  const unsigned long long T = 1ull << (a - b);
+  const unsigned long long units = T * (T - 1) / 2 + T;
+  if (units > 0xFFFFFFFFull)
+    return set_error(BREV_ERR_UNSUPPORTED, "too many tile pairs for one launch");
+  d.units = (unsigned)units;
+  const unsigned long long unit_bytes = 2ull * ((unsigned long long)E << (2 * b));
+  d.grain = (unsigned)std::min<unsigned long long>(
+      std::max<unsigned long long>(1, BATCH_TICKET_BYTES / unit_bytes), units);
+  d.first_ticket = 0;
+  const unsigned long long tickets = (units + d.grain - 1) / d.grain;
+  // the descriptor travels by value; only the ticket counter needs
+  // stream-ordered device memory (so the call can be captured in a graph)
+  void* ws = nullptr;
+  cudaError_t e = cudaMallocAsync(&ws, 16, stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(BREV_ERR_OOM, "transposition workspace: %s", cudaGetErrorString(e));
+  }
+  auto* d_ticket = reinterpret_cast<unsigned long long*>(ws);
+  e = cudaMemsetAsync(d_ticket, 0, sizeof(unsigned long long), stream);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(ws, stream);
+    return cuda_error(e, "ticket reset");
+  }
+  brev_status st = launch_batched_kernel(nullptr, 0, tickets, d_ticket,
+                                         stage_unit_bytes(2 * b, E, b), stream, &d);
+  cudaFreeAsync(ws, stream);
+  return st;
 }
 
 }  // namespace brev

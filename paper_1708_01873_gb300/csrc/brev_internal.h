@@ -73,6 +73,11 @@ brev_status batched_launch_forced(const BatchItem* items, int count, int b,
 // out[0..return); the built-in choice in *def.  0 candidates: the array is
 // not run by the batched kernel.
 int batched_candidates(int k, int E, int* out, int* def);
+// In-place transposition of a square 2^a x 2^a matrix through the
+// pipelined batched kernel (one descriptor); needs E in {4, 8, 16}, 16-byte
+// alignment and a >= transpose_pipelined_b(E).
+int transpose_pipelined_b(int E);
+brev_status transpose_inplace_pipelined(void* data, int a, int E, cudaStream_t stream);
 // Tuned batched tile exponent for (k, E), or -1 (brev_api.cu).
 int tuned_batched_b(int k, int E);
 // Argument checks of a batch (sizes, alignment, device ranges, no overlap).

@@ -185,6 +185,7 @@ def test_host_path(brev_lib, oracle_lib, cuda_device):
 
 def test_autotune_and_cache(brev_lib, oracle_lib, cuda_device, tmp_path):
     path = str(tmp_path / "tune.json")
+    brev_lib.brev_reset_tuning()  # only what this call tunes ends up in the file
     brev_lib.brev_autotune(12, 16, 8, path)
     import json
     d = json.load(open(path))
@@ -220,3 +221,4 @@ def test_autotune_and_cache(brev_lib, oracle_lib, cuda_device, tmp_path):
         assert_bytes_equal(to_bytes(out), oracle_lib.brev_oop(host_array(90 + k, k, 8), k, 8),
                            8, f"tuned k={k}")
     brev_lib.brev_reset_tuning()
+    brev_lib.brev_load_tune_cache(brev_lib.DEFAULT_TUNE_CACHE)  # the state later tests expect

@@ -27,7 +27,7 @@ def test_transpose_out_of_place(brev_lib, oracle_lib, cuda_device, E):
 
 @pytest.mark.parametrize("E", ES)
 def test_transpose_in_place_square(brev_lib, oracle_lib, cuda_device, E):
-    for a in (0, 1, 2, 4, 5, 8, 11):
+    for a in (0, 1, 2, 4, 5, 6, 7, 8, 9, 11):
         seed = 300 + a + E
         buf = device_array(seed, 2 * a, E)
         brev_lib.brev_transpose(buf, buf, a, a)
@@ -108,6 +108,43 @@ def test_transpose_full_size_twice_identity(brev_lib, cuda_device):
         back = torch.empty_like(src)
         brev_lib.brev_transpose(back, t, c, a)
         assert torch.equal(back.view(torch.uint8), src.view(torch.uint8))
+
+
+def test_transpose_in_place_full_size_equals_out_of_place(brev_lib, cuda_device):
+    """16384 x 16384 complex<double> (4 GiB) and 8192 x 8192 float32 in
+    place (the pipelined tile-pair kernel) against the out-of-place
+    transposition, then in place again back to the input."""
+    for a, E in ((14, 16), (13, 4)):
+        src = device_array(970 + a, 2 * a, E)
+        ref = torch.empty_like(src)
+        brev_lib.brev_transpose(ref, src, a, a)
+        buf = src.clone()
+        brev_lib.brev_transpose(buf, buf, a, a)
+        assert torch.equal(buf.view(torch.uint8), ref.view(torch.uint8)), (a, E)
+        brev_lib.brev_transpose(buf, buf, a, a)
+        assert torch.equal(buf.view(torch.uint8), src.view(torch.uint8)), (a, E)
+        del src, ref, buf
+    assert brev_lib.brev_wait_timeouts() == 0
+
+
+def test_transpose_in_place_captured_in_graph(brev_lib, oracle_lib, cuda_device):
+    """The in-place transposition enqueues only capturable work (a
+    stream-ordered allocation, a memset and the kernel): capture it once,
+    replay twice (the second replay restores the input)."""
+    a, E = 9, 8
+    buf = device_array(990, 2 * a, E)
+    h = host_array(990, 2 * a, E)
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=s, capture_error_mode="thread_local"):
+        brev_lib.brev_transpose(buf, buf, a, a, stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    assert_bytes_equal(to_bytes(buf), oracle_lib.transpose(h, a, a, E), E, "replay 1")
+    g.replay()
+    torch.cuda.synchronize()
+    assert_bytes_equal(to_bytes(buf), h, E, "replay 2")
 
 
 def test_transpose_errors(brev_lib, cuda_device):

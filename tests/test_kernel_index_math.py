@@ -280,13 +280,15 @@ def batched_stage_bytes(k, E, b):
     return (raw + 127) & ~127
 
 
-def emulate_staged_unit(E, b, k, u, nthr=256):
+def emulate_staged_unit(E, b, k, u, nthr=256, transpose=False):
     """Replay one unit of the TMA-staged batched kernel: the bulk copies
-    warp 0 issues (row x of each tile to padded row rev(x)) and the store
-    phase of all threads.  Returns (copied source elements, stores as
-    (destination element, source element), read-slot conflicts)."""
-    n = 1 << k
-    stage = batched_stage_bytes(k, E, b)
+    the producer warp issues (row x of each tile to padded row rev(x), or x
+    for a transposition) and the store phase of the consumer threads.
+    Bit reversal: an array of 2^k elements; transposition: a 2^k x 2^k
+    matrix.  Returns (copied source elements, stores as (destination
+    element, source element), read-slot conflicts)."""
+    n = 1 << (2 * k if transpose else k)
+    stage = batched_stage_bytes(2 * b if transpose else k, E, b)
     smem = {}  # byte offset of an element in the stage -> source element
     loads, stores, conflicts = [], [], 0
     if b == 0:
@@ -298,22 +300,38 @@ def emulate_staged_unit(E, b, k, u, nthr=256):
         for j in range(n):
             stores.append((j, smem[brev(j, k) * E]))
         return loads, stores, 0
-    wy = k - 2 * b
-    npairs = count_lt(wy)
-    if u < npairs:
-        y = unrank_lt(u, wy)
-        ry, nt = brev(y, wy), 2
-    else:
-        y = unrank_self(u - npairs, wy)
-        ry, nt = y, 1
     rowb, rows = E << b, 1 << b
     pitch = rowb + 16
-    stride = E << (k - b)
-    a_off, r_off = (y << b) * E, (ry << b) * E
+    if transpose:
+        T = 1 << (k - b)
+        npairs = T * (T - 1) // 2
+        if T >= 8:
+            tr, tc = blocked_upper(u, T)
+        elif u < npairs:
+            tr, tc = unrank_upper(u)
+        else:
+            tr = tc = u - npairs
+        nt = 1 if tr == tc else 2
+        stride = E << k
+        a_off = ((tr << (b + k)) + (tc << b)) * E
+        r_off = ((tc << (b + k)) + (tr << b)) * E
+        rmap = lambda x: x
+    else:
+        wy = k - 2 * b
+        npairs = count_lt(wy)
+        if u < npairs:
+            y = unrank_lt(u, wy)
+            ry, nt = brev(y, wy), 2
+        else:
+            y = unrank_self(u - npairs, wy)
+            ry, nt = y, 1
+        stride = E << (k - b)
+        a_off, r_off = (y << b) * E, (ry << b) * E
+        rmap = lambda x: brev(x, b)
     tx = 0
     for q in range(nt * rows):
         t, x = q >> b, q & (rows - 1)
-        dst = t * rows * pitch + brev(x, b) * pitch
+        dst = t * rows * pitch + rmap(x) * pitch
         src = (r_off if t else a_off) + x * stride
         assert dst % 16 == 0 and src % 16 == 0 and rowb % 16 == 0
         assert 0 <= dst and dst + rowb <= stage and 0 <= src and src + rowb <= n * E
@@ -343,7 +361,7 @@ def emulate_staged_unit(E, b, k, u, nthr=256):
                 blk.append([smem[addr + e * E] for e in range(V)])
                 reads.setdefault((q // 32, j), []).append((q % nthr, addr // 16))
             for e in range(V):
-                Z = brev(c * V + e, b)
+                Z = rmap(c * V + e)
                 g = dst_tile + Z * stride + d * 16
                 assert g % 16 == 0 and g + 16 <= n * E
                 for j in range(V):
@@ -375,6 +393,22 @@ def test_batched_staged_index_math(E):
             conf += c
         check_result(k, loads, stores)
         assert conf == 0, (E, b, k)
+    # the same pipeline as an in-place square transposition (2^a x 2^a)
+    b = {16: 5, 8: 5, 4: 6}[E]
+    for a in (b, b + 1, b + 3, b + 4):
+        T = 1 << (a - b)
+        loads, stores, conf = [], [], 0
+        for u in range(T * (T - 1) // 2 + T):
+            lo, st, c = emulate_staged_unit(E, b, a, u, transpose=True)
+            loads += lo
+            stores += st
+            conf += c
+        n = 1 << (2 * a)
+        assert sorted(loads) == list(range(n))
+        assert sorted(g for g, _ in stores) == list(range(n))
+        side = 1 << a
+        assert all(src == (g % side) * side + g // side for g, src in stores), (E, a)
+        assert conf == 0
     # two stages of the largest unit leave room for three CTAs per SM
     worst = max(batched_stage_bytes(2 * b, E, b) for b in BATCHED_SHAPES[E])
     assert 3 * (2 * worst + 1024 + 128) <= 228 * 1024
