@@ -218,28 +218,49 @@ BREV_API brev_status brev_fft_stages(void *dst, const void *src, int log2n, int 
  *     them on the device.
  *   - Completion: a CUDA event per batch; completion times are read on the
  *     device clock and each request's memory and slot are released.
+ * Resident mode (resident = 1) replaces the launches: one kernel stays on
+ * the GPU for the whole run and takes requests from a ring in page-locked
+ * host memory (NVLink-C2C), so no request pays a kernel launch:
+ *   - admission is the same (FIFO head, slots, pool), plus room in the ring
+ *     (4096 requests) and in the kernel's ticket window (2^22 tickets);
+ *   - each admitted request is written into the ring and published at once;
+ *     the kernel spreads its tile units over all CTAs (~64 KiB tickets), so
+ *     requests in flight overlap on the device;
+ *   - the kernel writes a completion word per request into host memory; its
+ *     completion time is when the serving thread sees that word;
+ *   - element sizes 4, 8 and 16 only (BREV_ERR_UNSUPPORTED otherwise);
+ *     max_batch and n_streams are not used.
+ *   The kernel's waits are bounded: if the run stalls for 2 s with nothing
+ *   to do (no request and no end of run), it exits, the waits are counted
+ *   in brev_wait_timeouts, and the run returns BREV_ERR_CUDA.
  * The arena is a caller-owned device buffer (256-byte aligned); the server
  * owns its streams and events. */
 typedef struct brev_server brev_server;
 typedef struct brev_server_config {
-    int max_slots; /* requests admitted at once */
+    int max_slots; /* requests admitted at once (resident: at most 4096) */
     int max_batch; /* requests per launch */
     int n_streams; /* streams with a batch in flight, 1..64 */
+    int resident;  /* 1: resident kernel fed through host memory, 0: launches */
 } brev_server_config;
 typedef struct brev_server_stats {
     uint64_t offered, completed, batches, launches;
-    double p50_us, p99_us, max_us, mean_us; /* device completion - arrival */
-    double queue_p99_us;                    /* launch - arrival */
+    double p50_us, p99_us, max_us, mean_us; /* completion - arrival: device clock
+                                             * (launches), serving thread's
+                                             * clock (resident) */
+    double queue_p99_us;                    /* launch or publication - arrival */
     double req_per_s, gbs, wall_s;          /* gbs: 2 n E bytes per request / wall time */
     uint64_t peak_pool_bytes;
     int max_inflight;
+    double host_p50_us, host_p99_us;        /* completion seen by the serving
+                                             * thread - arrival (both modes) */
 } brev_server_stats;
 typedef struct brev_server_request {
     uint64_t offset; /* byte offset of the request's buffer in the arena */
     int log2n, elem_bytes, batch;
     double arrival_us, launch_us, done_us; /* since the run started; launch: host
-                                            * time of the enqueue, done: device
-                                            * completion */
+                                            * time of the enqueue (publication
+                                            * when resident), done: completion as
+                                            * in p50_us */
 } brev_server_request;
 
 BREV_API brev_status brev_server_create(const brev_server_config *cfg, void *arena,

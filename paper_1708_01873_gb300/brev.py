@@ -38,7 +38,7 @@ class DeviceInfo(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("max_slots", ctypes.c_int), ("max_batch", ctypes.c_int),
-                ("n_streams", ctypes.c_int)]
+                ("n_streams", ctypes.c_int), ("resident", ctypes.c_int)]
 
 
 class ServerStats(ctypes.Structure):
@@ -48,7 +48,8 @@ class ServerStats(ctypes.Structure):
                 ("max_us", ctypes.c_double), ("mean_us", ctypes.c_double),
                 ("queue_p99_us", ctypes.c_double), ("req_per_s", ctypes.c_double),
                 ("gbs", ctypes.c_double), ("wall_s", ctypes.c_double),
-                ("peak_pool_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_int)]
+                ("peak_pool_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_int),
+                ("host_p50_us", ctypes.c_double), ("host_p99_us", ctypes.c_double)]
 
 
 class ServerRequest(ctypes.Structure):
@@ -334,10 +335,13 @@ def brev_fft_stages(dst, src, stages: int, inverse: bool = False, stream=None) -
 def brev_server_run_poisson(arena, seed: int, rate_per_s: float, seconds: float,
                             k_range=(10, 24), elem_sizes=(4, 8, 16), max_slots: int = 256,
                             max_batch: int = 256, n_streams: int = 4,
-                            hold_results: bool = False, trace: bool = False):
+                            hold_results: bool = False, trace: bool = False,
+                            resident: bool = False):
     """Run the native serving loop over the device tensor ``arena`` for a
-    seeded Poisson stream; returns (stats dict, trace list or None)."""
-    cfg = ServerConfig(max_slots, max_batch, n_streams)
+    seeded Poisson stream; returns (stats dict, trace list or None).
+    resident: one kernel fed through page-locked host memory instead of a
+    launch per batch."""
+    cfg = ServerConfig(max_slots, max_batch, n_streams, int(bool(resident)))
     h = ctypes.c_void_p()
     _check(lib().brev_server_create(ctypes.byref(cfg), arena.data_ptr(),
                                     arena.numel() * arena.element_size(), ctypes.byref(h)),

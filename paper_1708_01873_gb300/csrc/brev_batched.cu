@@ -107,6 +107,11 @@ struct StageInfo {
   unsigned long long stride;  // tile row stride in bytes
   int E, b, k, nt;
   int rev;                    // 1: bit-reversed row and column maps, 0: identity
+  // resident serving only: ring slot of the unit's request (-1 in a batch),
+  // the request's unit count and sequence number (completion accounting)
+  int slot;
+  unsigned req_units;
+  unsigned long long seq;
 };
 
 __host__ __device__ constexpr unsigned padded_row_bytes(int E, int b) {
@@ -129,13 +134,17 @@ __device__ unsigned g_batched_wait_timeouts;
 // consumers, who read it after the phase completes); all lanes then issue
 // the row copies, which complete on `full`.
 __device__ __forceinline__ void issue_unit(const BatchDesc& d, unsigned u, StageInfo* info,
-                                           unsigned char* buf, uint64_t* full) {
+                                           unsigned char* buf, uint64_t* full, int slot = -1,
+                                           unsigned long long seq = 0) {
   const int lane = threadIdx.x & 31;
   StageInfo s;
   s.E = d.E;
   s.b = d.b;
   s.k = d.k;
   s.rev = d.mode == BATCH_BITREV;
+  s.slot = slot;
+  s.req_units = d.units;
+  s.seq = seq;
   if (d.b == 0) {
     const uint32_t bytes = (uint32_t)d.E << d.k;
     s.a = s.r = d.ptr;
@@ -354,6 +363,249 @@ __global__ void __launch_bounds__(BATCH_BLOCK, BREV_BATCHED_MIN_CTAS)
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[st]);
+  }
+}
+
+// ------------------------------------------------ resident serving --
+// One kernel stays resident for a whole serving run and takes requests
+// from page-locked host memory, so no request pays a kernel launch.
+//   host:        writes request r into ring slot r % ring (ServeHostReq),
+//                then release-stores the request count;
+//   dispatcher:  (one warp, CTA 0) acquires the count, copies new requests
+//                into the device ring, fills the ticket table (ticket ->
+//                slot), then release-stores the published ticket count;
+//   producers:   claim a ticket with atomicAdd, wait until it is
+//                published, and run its units through the pipeline;
+//   consumers:   after storing their share of a unit, count it on the
+//                request's slot; the warp whose count completes the
+//                request writes seq + 1 into the host's done word.
+// Every wait is bounded (idle_ns of device time, then counted in
+// g_batched_wait_timeouts); the host's stop word ends the run.
+struct ServeDesc {  // device copy of a published request
+  char* ptr;
+  unsigned long long first_ticket;
+  unsigned units, grain;
+  int k, E, b, slot;
+  unsigned long long seq;
+};
+struct ServeCtl {  // device memory, zeroed before each launch
+  unsigned long long ticket;     // next ticket to claim
+  unsigned long long published;  // tickets published by the dispatcher
+  int stop;                      // the dispatcher saw the host's stop (or gave up)
+  int pad_;
+};
+struct ServeArgs {
+  ServeDesc* d_ring;
+  unsigned* d_done;  // per slot: units completed, counted per consumer warp
+  int* d_treq;       // ticket table: ticket & (ticket_table - 1) -> slot
+  ServeCtl* ctl;
+  const ServeHostReq* h_ring;
+  const ServeHostCtl* h_ctl;
+  unsigned long long* h_done;
+  unsigned ring, ticket_table, stage_bytes;
+  unsigned long long idle_ns;
+};
+
+constexpr int SERVE_BLOCK = BATCH_BLOCK + 32;  // consumers, producer, dispatcher
+
+// Dispatcher warp: host ring -> device ring and ticket table.
+__device__ void serve_dispatch(const ServeArgs& A) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long seen = 0, last = global_ns();
+  for (;;) {
+    unsigned long long n = 0;
+    if (lane == 0) n = ld_acquire_sys(&A.h_ctl->requests);
+    n = __shfl_sync(0xffffffffu, n, 0);
+    __syncwarp();  // orders the lanes' reads below after lane 0's acquire
+    if (n > seen) {
+      unsigned long long published = 0;
+      for (unsigned long long r = seen; r < n; ++r) {
+        const unsigned slot = (unsigned)(r & (A.ring - 1));
+        const volatile ServeHostReq* hr = A.h_ring + slot;
+        ServeDesc sd;
+        sd.ptr = hr->ptr;
+        sd.units = hr->units;
+        sd.grain = hr->grain;
+        sd.k = hr->k;
+        sd.E = hr->E;
+        sd.b = hr->b;
+        sd.seq = hr->seq;
+        sd.first_ticket = hr->first_ticket;
+        sd.slot = (int)slot;
+        const unsigned tickets = (sd.units + sd.grain - 1) / sd.grain;
+        if (lane == 0) {
+          A.d_ring[slot] = sd;
+          A.d_done[slot] = 0;
+        }
+        for (unsigned t = lane; t < tickets; t += 32)
+          A.d_treq[(sd.first_ticket + t) & (A.ticket_table - 1)] = (int)slot;
+        published = sd.first_ticket + tickets;
+      }
+      __threadfence();
+      __syncwarp();
+      if (lane == 0) st_release_gpu(&A.ctl->published, published);
+      seen = n;
+      last = global_ns();
+      continue;
+    }
+    int stop = 0;
+    if (lane == 0) stop = ld_acquire_sys(&A.h_ctl->stop);
+    stop = __shfl_sync(0xffffffffu, stop, 0);
+    const bool idle = global_ns() - last > A.idle_ns;
+    if (stop || idle) {
+      if (lane == 0) {
+        if (!stop) atomicAdd(&g_batched_wait_timeouts, 1u);
+        st_release_gpu(&A.ctl->stop, 1);
+      }
+      return;
+    }
+  }
+}
+
+// Producer: claim the next ticket and wait until it is published.
+// Returns 1 with (d, u, ulast, slot, seq) set, 0 at the end of the run,
+// -1 after idle_ns without it being published or the run ending.
+__device__ __forceinline__ int serve_next_ticket(const ServeArgs& A, BatchDesc& d, unsigned& u,
+                                                 unsigned& ulast, int& slot,
+                                                 unsigned long long& seq) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long t = 0;
+  int status = 0;
+  if (lane == 0) {
+    t = atomicAdd(&A.ctl->ticket, 1ull);
+    const unsigned long long t0 = global_ns();
+    unsigned ns = 32;
+    for (;;) {
+      if (ld_acquire_gpu(&A.ctl->published) > t) {
+        status = 1;
+        break;
+      }
+      if (ld_acquire_gpu(&A.ctl->stop)) {  // published is final once stop is set
+        status = ld_acquire_gpu(&A.ctl->published) > t ? 1 : 0;
+        break;
+      }
+      if (global_ns() - t0 > A.idle_ns) {
+        status = -1;
+        break;
+      }
+      __nanosleep(ns);
+      if (ns < 256) ns *= 2;
+    }
+  }
+  status = __shfl_sync(0xffffffffu, status, 0);
+  if (status <= 0) return status;
+  t = __shfl_sync(0xffffffffu, t, 0);
+  __syncwarp();  // the lanes' reads below come after lane 0's acquire
+  // read through L2 (a slot's previous request may sit in this SM's L1)
+  const int sl = __ldcg(A.d_treq + (t & (A.ticket_table - 1)));
+  const ServeDesc* p = A.d_ring + sl;
+  d.ptr = (char*)__ldcg((const unsigned long long*)&p->ptr);
+  d.first_ticket = __ldcg(&p->first_ticket);
+  d.units = __ldcg(&p->units);
+  d.grain = __ldcg(&p->grain);
+  d.k = __ldcg(&p->k);
+  d.E = __ldcg(&p->E);
+  d.b = __ldcg(&p->b);
+  d.mode = BATCH_BITREV;
+  seq = __ldcg(&p->seq);
+  slot = sl;
+  u = (unsigned)(t - d.first_ticket) * d.grain;
+  ulast = min(u + d.grain, d.units);
+  // the request's buffer may hold an earlier request's stores (generic
+  // proxy), made visible through the acquire chain; the copies that read it
+  // are async-proxy operations
+  fence_proxy_async_global();
+  return 1;
+}
+
+__global__ void __launch_bounds__(SERVE_BLOCK, BREV_BATCHED_MIN_CTAS)
+    k_serve(const ServeArgs A) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full[BATCH_STAGES], empty[BATCH_STAGES];
+  __shared__ StageInfo info[BATCH_STAGES];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    for (int i = 0; i < BATCH_STAGES; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], BATCH_CONSUMER_WARPS);
+    }
+    mbar_init_fence();
+  }
+  __syncthreads();  // barriers initialised (every warp takes part before the roles split)
+
+  if (warp == BATCH_CONSUMER_WARPS + 1) {  // dispatcher (CTA 0 only)
+    if (blockIdx.x == 0) serve_dispatch(A);
+    return;
+  }
+  if (warp == BATCH_CONSUMER_WARPS) {  // producer
+    int slot = -1;
+    unsigned u = 0, ulast = 0;
+    unsigned long long seq = 0;
+    BatchDesc d{};
+    unsigned i = 0;
+    bool ok = true, marker = false;
+#pragma unroll 1
+    for (;; ++i) {
+      const int st = i % BATCH_STAGES;
+      if (i >= BATCH_STAGES) {
+        ok = mbar_wait_bounded(&empty[st], (i / BATCH_STAGES - 1) & 1);
+        if (!ok) break;
+        fence_proxy_async_smem();
+      }
+      int more = 1;
+      if (slot >= 0 && u + 1 < ulast) {
+        ++u;
+      } else {
+        more = serve_next_ticket(A, d, u, ulast, slot, seq);
+        if (more < 0) ok = false;
+      }
+      if (more <= 0) {  // end marker: a phase with no bytes
+        if (lane == 0) {
+          info[st].nt = -1;
+          mbar_arrive(&full[st]);
+        }
+        marker = true;
+        break;
+      }
+      issue_unit(d, u, &info[st], smem + (size_t)st * A.stage_bytes, &full[st], slot, seq);
+    }
+    if (!ok && lane == 0) atomicAdd(&g_batched_wait_timeouts, 1u);
+    // as in k_batched: the copies still in flight land before the CTA
+    // exits; after an end marker, unit i-S's barrier has moved on to the
+    // marker's phase and is not waited on
+    const unsigned back = marker ? BATCH_STAGES - 1 : BATCH_STAGES;
+    for (unsigned m = 1; m <= back && m <= i; ++m) {
+      const unsigned j = i - m;
+      mbar_wait_bounded(&full[j % BATCH_STAGES], (j / BATCH_STAGES) & 1);
+    }
+    return;
+  }
+  // consumers
+#pragma unroll 1
+  for (unsigned i = 0;; ++i) {
+    const int st = i % BATCH_STAGES;
+    if (!mbar_wait_bounded(&full[st], (i / BATCH_STAGES) & 1)) {
+      if (lane == 0) atomicAdd(&g_batched_wait_timeouts, 1u);
+      return;
+    }
+    const StageInfo s = info[st];
+    if (s.nt < 0) return;
+    const unsigned char* buf = smem + (size_t)st * A.stage_bytes;
+    switch (s.E) {
+      case 16: store_staged_unit<16>(buf, s.a, s.r, s.stride, s.b, s.k, s.nt, s.rev); break;
+      case 8: store_staged_unit<8>(buf, s.a, s.r, s.stride, s.b, s.k, s.nt, s.rev); break;
+      case 4: store_staged_unit<4>(buf, s.a, s.r, s.stride, s.b, s.k, s.nt, s.rev); break;
+    }
+    // count the warp's share of the unit: the warp barrier orders every
+    // lane's stores before lane 0's release; the warp that completes the
+    // request has acquired all the others' and releases the lot to the host
+    __syncwarp();
+    if (lane == 0) {
+      const unsigned need = (unsigned)BATCH_CONSUMER_WARPS * s.req_units;
+      if (atom_add_acq_rel_gpu(&A.d_done[s.slot], 1u) + 1u == need)
+        st_release_sys(&A.h_done[s.slot], s.seq + 1);
+      mbar_arrive(&empty[st]);
+    }
   }
 }
 
@@ -609,6 +861,121 @@ brev_status transpose_inplace_pipelined(void* data, int a, int E, cudaStream_t s
                                          stage_unit_bytes(2 * b, E, b), stream, &d);
   cudaFreeAsync(ws, stream);
   return st;
+}
+
+// ---------------------------------------------- resident serving, host --
+// A request's units are spread over about two tickets per resident CTA (a
+// request finishes soonest when all CTAs share it), with tickets of one
+// unit at least and of about 256 KiB at most.
+bool resident_shape(int k, int E, int ctas, int* b, unsigned* units, unsigned* grain) {
+  if (!(E == 4 || E == 8 || E == 16) || k <= 1 || k > BREV_MAX_LOG2N) return false;
+  const int bb = batched_b(k, E);
+  if (bb < 0) return false;
+  unsigned long long n_units, unit_bytes;
+  if (bb == 0) {
+    n_units = 1;
+    unit_bytes = (unsigned long long)E << k;
+  } else {
+    const int w = k - 2 * bb;
+    n_units = (unsigned long long)count_lt(w) + count_self(w);
+    unit_bytes = 2ull * ((unsigned long long)E << (2 * bb));
+  }
+  if (n_units > 0x7FFFFFFFull) return false;
+  *b = bb;
+  *units = (unsigned)n_units;
+  const unsigned long long max_grain =
+      std::max<unsigned long long>(1, BATCH_TICKET_BYTES / unit_bytes);
+  *grain = (unsigned)std::min<unsigned long long>(
+      std::max<unsigned long long>(1, n_units / (2ull * (unsigned long long)std::max(ctas, 1))),
+      max_grain);
+  return true;
+}
+
+// Stage size that holds any unit the resident kernel may meet (every
+// (E, b) the batched path accepts, and whole arrays of up to 32 KiB).
+static unsigned serve_stage_bytes() {
+  unsigned m = (unsigned)BATCH_WHOLE_MAX_BYTES;
+  for (int E : {4, 8, 16})
+    for (int b = 1; b <= 6; ++b)
+      if (batched_shape_ok(E, b)) m = std::max(m, stage_unit_bytes(2 * b, E, b));
+  return m;
+}
+
+brev_status resident_alloc(ResidentState* st, unsigned ring, unsigned ticket_table) {
+  if (!st || ring == 0 || (ring & (ring - 1)) || ticket_table == 0 ||
+      (ticket_table & (ticket_table - 1)))
+    return set_error(BREV_ERR_INVALID_ARG, "resident ring / ticket table sizes");
+  *st = ResidentState{};
+  st->ring = ring;
+  st->ticket_table = ticket_table;
+  cudaError_t e = cudaHostAlloc((void**)&st->h_ring, ring * sizeof(ServeHostReq),
+                                cudaHostAllocMapped | cudaHostAllocPortable);
+  if (e == cudaSuccess)
+    e = cudaHostAlloc((void**)&st->h_ctl, 256, cudaHostAllocMapped | cudaHostAllocPortable);
+  if (e == cudaSuccess)
+    e = cudaHostAlloc((void**)&st->h_done, ring * sizeof(unsigned long long),
+                      cudaHostAllocMapped | cudaHostAllocPortable);
+  const size_t dbytes = 256 + ring * sizeof(ServeDesc) + ring * sizeof(unsigned) +
+                        (size_t)ticket_table * sizeof(int);
+  if (e == cudaSuccess) e = cudaMalloc(&st->d_mem, dbytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    resident_free(st);
+    return set_error(BREV_ERR_OOM, "resident serving state: %s", cudaGetErrorString(e));
+  }
+  const unsigned smem = BATCH_STAGES * serve_stage_bytes();
+  e = ensure_smem((const void*)k_serve, smem);
+  int per_sm = 0;
+  if (e != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_serve, SERVE_BLOCK, smem) !=
+          cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  st->ctas = per_sm * current_device_sm_count();
+  return BREV_OK;
+}
+
+void resident_free(ResidentState* st) {
+  if (!st) return;
+  if (st->h_ring) cudaFreeHost(st->h_ring);
+  if (st->h_ctl) cudaFreeHost(st->h_ctl);
+  if (st->h_done) cudaFreeHost(st->h_done);
+  if (st->d_mem) cudaFree(st->d_mem);
+  *st = ResidentState{};
+}
+
+brev_status resident_launch(ResidentState* st, cudaStream_t stream,
+                            unsigned long long idle_ns) {
+  if (!st || !st->d_mem) return set_error(BREV_ERR_INVALID_ARG, "no resident state");
+  memset(st->h_ctl, 0, 256);
+  memset(st->h_done, 0, st->ring * sizeof(unsigned long long));
+  ServeArgs A{};
+  char* dm = (char*)st->d_mem;
+  A.ctl = (ServeCtl*)dm;
+  A.d_ring = (ServeDesc*)(dm + 256);
+  A.d_done = (unsigned*)(dm + 256 + st->ring * sizeof(ServeDesc));
+  A.d_treq = (int*)(dm + 256 + st->ring * (sizeof(ServeDesc) + sizeof(unsigned)));
+  cudaError_t e = cudaHostGetDevicePointer((void**)&A.h_ring, st->h_ring, 0);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&A.h_ctl, st->h_ctl, 0);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&A.h_done, st->h_done, 0);
+  if (e != cudaSuccess) return cuda_error(e, "device view of the serving ring");
+  A.ring = st->ring;
+  A.ticket_table = st->ticket_table;
+  A.stage_bytes = serve_stage_bytes();
+  A.idle_ns = idle_ns;
+  e = cudaMemsetAsync(A.ctl, 0, sizeof(ServeCtl), stream);
+  if (e != cudaSuccess) return cuda_error(e, "serving control reset");
+  const unsigned smem = BATCH_STAGES * A.stage_bytes;
+  e = ensure_smem((const void*)k_serve, smem);
+  if (e != cudaSuccess) return cuda_error(e, "shared-memory limit of the serving kernel");
+  void* args[] = {(void*)&A};
+  e = cudaLaunchKernel((const void*)k_serve, dim3(std::max(st->ctas, 1)), dim3(SERVE_BLOCK),
+                       args, smem, stream);
+  if (e != cudaSuccess) return cuda_error(e, "serving kernel launch");
+  note_launch();
+  return BREV_OK;
 }
 
 }  // namespace brev

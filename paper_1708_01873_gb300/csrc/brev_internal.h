@@ -78,6 +78,46 @@ int batched_candidates(int k, int E, int* out, int* def);
 // alignment and a >= transpose_pipelined_b(E).
 int transpose_pipelined_b(int E);
 brev_status transpose_inplace_pipelined(void* data, int a, int E, cudaStream_t stream);
+// ---- resident serving (kernel in brev_batched.cu, host loop in brev_serve.cu)
+// One request, written by the host into page-locked memory before it
+// publishes the request count.
+struct ServeHostReq {
+  char* ptr;
+  unsigned units;  // work units (tile pairs, self tiles, or 1 whole array)
+  unsigned grain;  // units per ticket
+  int k, E, b, pad_;
+  unsigned long long seq;           // request number (the slot is seq % ring)
+  unsigned long long first_ticket;  // tickets [first_ticket, + ceil(units / grain))
+};
+// Host-written control words (page-locked).
+struct ServeHostCtl {
+  unsigned long long requests;  // requests published so far
+  int stop;                     // 1: no more requests; the kernel drains and exits
+  int pad_;
+};
+struct ResidentState {
+  // page-locked host memory, read and written by the running kernel
+  ServeHostReq* h_ring = nullptr;
+  ServeHostCtl* h_ctl = nullptr;
+  unsigned long long* h_done = nullptr;  // per slot: seq + 1 of its last completed request
+  // device memory: descriptor ring, per-slot unit counters, ticket table,
+  // ticket counters
+  void* d_mem = nullptr;
+  unsigned ring = 0, ticket_table = 0;
+  int ctas = 0;  // resident CTAs of the kernel (SMs x occupancy)
+};
+// Allocate the state for `ring` request slots and a ticket table of
+// `ticket_table` entries (both powers of two).
+brev_status resident_alloc(ResidentState* st, unsigned ring, unsigned ticket_table);
+void resident_free(ResidentState* st);
+// Reset the counters and control words (stream-ordered for the device
+// part) and launch the resident kernel on `stream`; it runs until the host
+// sets h_ctl->stop (or until idle_ns pass with no new request, counted as a
+// wait timeout).
+brev_status resident_launch(ResidentState* st, cudaStream_t stream, unsigned long long idle_ns);
+// Units, grain and tile exponent of a request in the resident kernel;
+// false if it cannot run there (elem sizes 1, 2; k <= 1).
+bool resident_shape(int k, int E, int ctas, int* b, unsigned* units, unsigned* grain);
 // Tuned batched tile exponent for (k, E), or -1 (brev_api.cu).
 int tuned_batched_b(int k, int E);
 // Argument checks of a batch (sizes, alignment, device ranges, no overlap).

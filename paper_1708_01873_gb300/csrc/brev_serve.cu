@@ -15,6 +15,16 @@
 //     is read on the device clock (elapsed time from a reference event
 //     recorded when the run starts) and its memory and slot are released.
 // Latency = device completion time - arrival time.
+//
+// Resident mode (cfg.resident): the same admission policy, but no launch
+// per request.  One kernel (resident_launch) stays on the GPU for the run;
+// each admitted request is written into a ring in page-locked host memory
+// and published at once; the kernel writes a completion word per request
+// into host memory, and latency = when the serving thread sees that word -
+// arrival time.  Besides slots and pool memory, admission needs a free ring
+// slot and room in the kernel's ticket window (the ticket table maps
+// ticket & (table - 1) to a ring slot, so the tickets between the oldest
+// request in flight and the newest must fit in the table).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -84,9 +94,15 @@ struct Req {
   double arrival;  // seconds since the run started
   uint64_t offset = 0;
   double launch = 0, done = 0;
+  double seen = 0;  // completion as seen by the serving thread
   int batch = -1;
   bool admitted = false;
 };
+
+constexpr unsigned kResidentRing = 4096;
+constexpr unsigned kResidentTickets = 1u << 22;
+constexpr unsigned long long kResidentIdleNs = 2000000000ull;
+constexpr double kResidentStopIdle = 0.5;  // seconds
 
 struct Inflight {
   cudaEvent_t ev;
@@ -122,7 +138,214 @@ struct brev_server {
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> spare_events;
   int device = 0;
+  brev::ResidentState res;  // resident mode only
 };
+
+namespace {
+
+// Statistics and trace of a finished run (both modes).
+void finish_stats(const std::vector<Req>& reqs, const std::vector<double>& lat_us,
+                  const std::vector<double>& queue_us, uint64_t completed, uint64_t bytes_moved,
+                  uint64_t batches, uint64_t launches, uint64_t peak_pool, int max_inflight,
+                  double wall, brev_server_request* trace, uint64_t trace_capacity,
+                  brev_server_stats* out) {
+  out->completed = completed;
+  out->batches = batches;
+  out->launches = launches;
+  out->p50_us = percentile(lat_us, 50);
+  out->p99_us = percentile(lat_us, 99);
+  out->max_us = lat_us.empty() ? 0 : *std::max_element(lat_us.begin(), lat_us.end());
+  double sum = 0;
+  for (double v : lat_us) sum += v;
+  out->mean_us = lat_us.empty() ? 0 : sum / (double)lat_us.size();
+  out->queue_p99_us = percentile(queue_us, 99);
+  std::vector<double> host_us;
+  host_us.reserve(reqs.size());
+  for (const Req& r : reqs)
+    if (r.seen > 0) host_us.push_back((r.seen - r.arrival) * 1e6);
+  out->host_p50_us = percentile(host_us, 50);
+  out->host_p99_us = percentile(host_us, 99);
+  out->wall_s = wall;
+  out->req_per_s = (double)completed / wall;
+  out->gbs = (double)bytes_moved / wall / 1e9;
+  out->peak_pool_bytes = peak_pool;
+  out->max_inflight = max_inflight;
+  out->offered = (uint64_t)reqs.size();
+  if (trace) {
+    for (uint64_t i = 0; i < reqs.size() && i < trace_capacity; ++i) {
+      trace[i].offset = reqs[i].offset;
+      trace[i].log2n = reqs[i].k;
+      trace[i].elem_bytes = reqs[i].E;
+      trace[i].batch = reqs[i].batch;
+      trace[i].arrival_us = reqs[i].arrival * 1e6;
+      trace[i].launch_us = reqs[i].launch * 1e6;
+      trace[i].done_us = reqs[i].done * 1e6;
+    }
+  }
+}
+
+// Resident mode: see the comment at the top of the file.
+brev_status run_resident(brev_server* srv, std::vector<Req>& reqs, int hold_results,
+                         brev_server_request* trace, uint64_t trace_capacity,
+                         brev_server_stats* out) {
+  using namespace brev;
+  ResidentState& R = srv->res;
+  Pool pool(srv->arena_bytes);
+  struct Live {
+    size_t req;
+    unsigned long long seq, first_ticket;
+  };
+  std::deque<size_t> waiting;
+  std::vector<Live> live;                      // requests in flight
+  std::map<unsigned long long, int> firsts;    // first tickets in flight (count)
+  std::vector<double> lat_us, queue_us;
+  lat_us.reserve(reqs.size());
+  queue_us.reserve(reqs.size());
+  uint64_t completed = 0, bytes_moved = 0, publications = 0;
+  unsigned long long next_seq = 0, tickets = 0;
+  int max_inflight = 0;
+  brev_status result = BREV_OK, s = BREV_OK;
+  const uint64_t launches0 = brev_launch_count();
+  cudaStream_t ks = srv->streams[0];
+
+  // the kernel does not wait on other streams: finish earlier device work
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_error(e, "device synchronize before serving");
+  const Clock::time_point t0 = Clock::now();
+  auto now_s = [&] { return std::chrono::duration<double>(Clock::now() - t0).count(); };
+  // The kernel runs while there is traffic.  After kResidentStopIdle s with
+  // nothing in flight or waiting, the host stops it (so its own 2 s limit
+  // only fires if this thread stalls); the next request launches it again,
+  // with sequence numbers and tickets counted from 0.
+  bool running = false;
+  double last_busy = 0;
+  auto stop_kernel = [&]() -> cudaError_t {
+    __atomic_store_n(&R.h_ctl->stop, 1, __ATOMIC_RELEASE);
+    running = false;
+    return cudaStreamSynchronize(ks);
+  };
+
+  size_t next_arrival = 0;
+  while (result == BREV_OK && (next_arrival < reqs.size() || !waiting.empty() || !live.empty())) {
+    const double now = now_s();
+    while (next_arrival < reqs.size() && reqs[next_arrival].arrival <= now)
+      waiting.push_back(next_arrival++);
+    // completions: the kernel wrote seq + 1 into the slot's done word
+    for (size_t i = 0; i < live.size();) {
+      const unsigned slot = (unsigned)(live[i].seq & (R.ring - 1));
+      if (__atomic_load_n(&R.h_done[slot], __ATOMIC_ACQUIRE) != live[i].seq + 1) {
+        ++i;
+        continue;
+      }
+      Req& r = reqs[live[i].req];
+      r.done = r.seen = now_s();
+      lat_us.push_back((r.done - r.arrival) * 1e6);
+      queue_us.push_back((r.launch - r.arrival) * 1e6);
+      bytes_moved += 2 * ((uint64_t)r.E << r.k);
+      ++completed;
+      if (!hold_results) pool.release(r.offset);
+      auto f = firsts.find(live[i].first_ticket);
+      if (--f->second == 0) firsts.erase(f);
+      live[i] = live.back();
+      live.pop_back();
+    }
+    if (!live.empty() || !waiting.empty()) last_busy = now;
+    if (running && live.empty() && waiting.empty() && now - last_busy > kResidentStopIdle) {
+      e = stop_kernel();
+      if (e != cudaSuccess) {
+        result = cuda_error(e, "resident serving kernel");
+        break;
+      }
+    }
+    // a kernel that ended with work outstanding gave up on a wait
+    if (!live.empty() && cudaStreamQuery(ks) != cudaErrorNotReady) {
+      cudaGetLastError();
+      result = set_error(BREV_ERR_CUDA,
+                         "the resident serving kernel stopped with %zu requests in flight "
+                         "(see brev_wait_timeouts)",
+                         live.size());
+      break;
+    }
+    // admission and publication
+    bool published = false;
+    while (!waiting.empty() && (int)live.size() < srv->cfg.max_slots) {
+      Req& r = reqs[waiting.front()];
+      int b = 0;
+      unsigned units = 0, grain = 1;
+      if (!resident_shape(r.k, r.E, R.ctas, &b, &units, &grain)) {
+        result = set_error(BREV_ERR_UNSUPPORTED, "request k=%d E=%d in resident mode", r.k, r.E);
+        break;
+      }
+      const unsigned long long nt = (units + grain - 1) / grain;
+      const unsigned long long oldest_seq = live.empty() ? next_seq : [&] {
+        unsigned long long m = next_seq;
+        for (const Live& l : live) m = std::min(m, l.seq);
+        return m;
+      }();
+      const unsigned long long oldest_ticket = firsts.empty() ? tickets : firsts.begin()->first;
+      if (next_seq - oldest_seq >= R.ring) break;  // ring slot still in use
+      if (nt > R.ticket_table) {
+        result = set_error(BREV_ERR_UNSUPPORTED, "request k=%d E=%d has more tickets than the "
+                           "resident kernel's window", r.k, r.E);
+        break;
+      }
+      if (tickets + nt - oldest_ticket > R.ticket_table) break;  // ticket window full
+      uint64_t off = 0;
+      if (!pool.alloc((uint64_t)r.E << r.k, &off)) {
+        if (hold_results && live.empty())
+          result = set_error(BREV_ERR_OOM, "arena too small to hold every result of the stream");
+        break;
+      }
+      if (!running) {  // (re)start: nothing is in flight, count from 0
+        next_seq = 0;
+        tickets = 0;
+        s = resident_launch(&R, ks, kResidentIdleNs);
+        if (s != BREV_OK) {
+          result = s;
+          break;
+        }
+        running = true;
+      }
+      r.offset = off;
+      r.admitted = true;
+      r.launch = now_s();
+      r.batch = (int)publications;
+      const unsigned slot = (unsigned)(next_seq & (R.ring - 1));
+      ServeHostReq& h = R.h_ring[slot];
+      h.ptr = srv->arena + off;
+      h.units = units;
+      h.grain = grain;
+      h.k = r.k;
+      h.E = r.E;
+      h.b = b;
+      h.seq = next_seq;
+      h.first_ticket = tickets;
+      live.push_back(Live{waiting.front(), next_seq, tickets});
+      ++firsts[tickets];
+      tickets += nt;
+      ++next_seq;
+      waiting.pop_front();
+      published = true;
+    }
+    if (result != BREV_OK) break;
+    if (published) {
+      __atomic_store_n(&R.h_ctl->requests, next_seq, __ATOMIC_RELEASE);
+      ++publications;
+      max_inflight = std::max(max_inflight, (int)live.size());
+    }
+  }
+  // end of the run: the kernel drains and exits
+  e = running ? stop_kernel() : cudaStreamSynchronize(ks);
+  const double wall = now_s();
+  if (e != cudaSuccess && result == BREV_OK) result = cuda_error(e, "resident serving kernel");
+  if (result != BREV_OK) return result;
+  finish_stats(reqs, lat_us, queue_us, completed, bytes_moved, publications,
+               brev_launch_count() - launches0, pool.peak, max_inflight, wall, trace,
+               trace_capacity, out);
+  return BREV_OK;
+}
+
+}  // namespace
 
 using namespace brev;
 
@@ -133,7 +356,8 @@ brev_status brev_server_create(const brev_server_config* cfg, void* arena, uint6
   if (!out) return set_error(BREV_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (!cfg || cfg->max_slots < 1 || cfg->max_batch < 1 || cfg->n_streams < 1 ||
-      cfg->n_streams > 64)
+      cfg->n_streams > 64 || (cfg->resident != 0 && cfg->resident != 1) ||
+      (cfg->resident && cfg->max_slots > (int)kResidentRing))
     return set_error(BREV_ERR_INVALID_ARG, "bad server configuration");
   if (!arena || arena_bytes == 0 || (uintptr_t)arena % 256)
     return set_error(BREV_ERR_INVALID_ARG, "arena must be a 256-byte aligned device buffer");
@@ -153,6 +377,13 @@ brev_status brev_server_create(const brev_server_config* cfg, void* arena, uint6
     }
     srv->streams.push_back(st);
   }
+  if (cfg->resident) {
+    s = resident_alloc(&srv->res, kResidentRing, kResidentTickets);
+    if (s != BREV_OK) {
+      brev_server_destroy(srv);
+      return s;
+    }
+  }
   srv->arena_bytes = arena_bytes;
   *out = srv;
   return BREV_OK;
@@ -165,6 +396,7 @@ void brev_server_destroy(brev_server* srv) {
     cudaStreamDestroy(st);
   }
   for (cudaEvent_t e : srv->spare_events) cudaEventDestroy(e);
+  resident_free(&srv->res);
   delete srv;
 }
 
@@ -201,6 +433,12 @@ brev_status brev_server_run_poisson(brev_server* srv, uint64_t seed, double rate
       r.arrival = t;
       reqs.push_back(r);
     }
+  }
+  if (srv->cfg.resident) {
+    for (int i = 0; i < n_elem_bytes; ++i)
+      if (!(elem_bytes[i] == 4 || elem_bytes[i] == 8 || elem_bytes[i] == 16))
+        return set_error(BREV_ERR_UNSUPPORTED, "resident mode serves 4-, 8- and 16-byte elements");
+    return run_resident(srv, reqs, hold_results, trace, trace_capacity, out);
   }
   Pool pool(srv->arena_bytes);
   std::deque<size_t> waiting, admitted;
@@ -256,9 +494,11 @@ brev_status brev_server_run_poisson(brev_server* srv, uint64_t seed, double rate
       float ms = 0;
       cudaEventElapsedTime(&ms, ref, inflight[i].ev);
       const double done = ms * 1e-3;
+      const double seen = now_s();
       for (size_t ri : inflight[i].reqs) {
         Req& r = reqs[ri];
         r.done = done;
+        r.seen = seen;
         lat_us.push_back((done - r.arrival) * 1e6);
         queue_us.push_back((r.launch - r.arrival) * 1e6);
         bytes_moved += 2 * ((uint64_t)r.E << r.k);
@@ -346,33 +586,9 @@ brev_status brev_server_run_poisson(brev_server* srv, uint64_t seed, double rate
   for (Inflight& f : inflight) srv->spare_events.push_back(f.ev);
   if (result != BREV_OK) return result;
 
-  out->completed = completed;
-  out->batches = (uint64_t)batches;
-  out->launches = brev_launch_count() - launches0;
-  out->p50_us = percentile(lat_us, 50);
-  out->p99_us = percentile(lat_us, 99);
-  out->max_us = lat_us.empty() ? 0 : *std::max_element(lat_us.begin(), lat_us.end());
-  double sum = 0;
-  for (double v : lat_us) sum += v;
-  out->mean_us = lat_us.empty() ? 0 : sum / (double)lat_us.size();
-  out->queue_p99_us = percentile(queue_us, 99);
-  out->wall_s = wall;
-  out->req_per_s = (double)completed / wall;
-  out->gbs = (double)bytes_moved / wall / 1e9;
-  out->peak_pool_bytes = pool.peak;
-  out->max_inflight = max_inflight;
-  out->offered = (uint64_t)reqs.size();
-  if (trace) {
-    for (uint64_t i = 0; i < reqs.size() && i < trace_capacity; ++i) {
-      trace[i].offset = reqs[i].offset;
-      trace[i].log2n = reqs[i].k;
-      trace[i].elem_bytes = reqs[i].E;
-      trace[i].batch = reqs[i].batch;
-      trace[i].arrival_us = reqs[i].arrival * 1e6;
-      trace[i].launch_us = reqs[i].launch * 1e6;
-      trace[i].done_us = reqs[i].done * 1e6;
-    }
-  }
+  finish_stats(reqs, lat_us, queue_us, completed, bytes_moved, (uint64_t)batches,
+               brev_launch_count() - launches0, pool.peak, max_inflight, wall, trace,
+               trace_capacity, out);
   return BREV_OK;
 }
 

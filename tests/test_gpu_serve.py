@@ -103,3 +103,71 @@ def test_native_server_production_mode(brev_lib, cuda_device):
     with pytest.raises(brev_lib.BrevError):   # hold mode that cannot fit: refused, no hang
         brev_lib.brev_server_run_poisson(arena[: 64 << 20], seed=1, rate_per_s=20000.0,
                                          seconds=0.2, k_range=(20, 22), hold_results=True)
+
+
+def _check_held_results(brev_lib, oracle_lib, arena, initial, trace, k_oracle=11):
+    for i, r in enumerate(trace):
+        E, k, off = r["elem_bytes"], r["log2n"], r["offset"]
+        nb = E << k
+        src = initial[off:off + nb].view(DTYPE[E])
+        alone = torch.empty_like(src)
+        brev_lib.brev_permute_to(alone, src)
+        got = arena[off:off + nb].cpu().numpy()
+        assert_bytes_equal(got, alone.view(torch.uint8).cpu().numpy(), E,
+                           f"request {i} k={k} E={E}: mix vs alone")
+        if k <= k_oracle:
+            exp = oracle_lib.brev_oop(initial[off:off + nb].cpu().numpy(), k, E)
+            assert_bytes_equal(got, exp, E, f"request {i}: vs oracle")
+        assert r["arrival_us"] <= r["launch_us"] <= r["done_us"]
+
+
+def test_resident_server_results_equal_alone(brev_lib, oracle_lib, cuda_device):
+    """Resident mode: one kernel fed through host memory serves a Poisson
+    stream (requests overlapping on the device); with results held, every
+    request's region equals the single-array permutation of its initial
+    bytes, and the oracle for the small ones."""
+    arena = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    inputs.fill_torch(arena, 98, "u8", chunk=1 << 26)
+    initial = arena.clone()
+    torch.cuda.synchronize()
+    stats, trace = brev_lib.brev_server_run_poisson(
+        arena, seed=9, rate_per_s=100000.0, seconds=0.015, k_range=(2, 17),
+        elem_sizes=(4, 8, 16), max_slots=32, hold_results=True, trace=True, resident=True)
+    torch.cuda.synchronize()
+    assert stats["completed"] == stats["offered"] == len(trace) > 1000
+    assert stats["launches"] == 1 and stats["max_inflight"] > 1   # overlapping requests
+    spans = sorted((r["offset"], r["offset"] + (r["elem_bytes"] << r["log2n"])) for r in trace)
+    assert all(a[1] <= b[0] for a, b in zip(spans, spans[1:]))
+    _check_held_results(brev_lib, oracle_lib, arena, initial, trace)
+    assert brev_lib.brev_wait_timeouts() == 0
+
+
+def test_resident_server_restarts_after_idle(brev_lib, oracle_lib, cuda_device):
+    """Arrivals further apart than the idle limit: the host stops the kernel
+    between them and launches it again; every result is still right."""
+    arena = torch.empty(64 << 20, dtype=torch.uint8, device="cuda")
+    inputs.fill_torch(arena, 97, "u8", chunk=1 << 26)
+    initial = arena.clone()
+    torch.cuda.synchronize()
+    stats, trace = brev_lib.brev_server_run_poisson(
+        arena, seed=3, rate_per_s=3.0, seconds=2.0, k_range=(8, 16), elem_sizes=(8, 16),
+        max_slots=8, hold_results=True, trace=True, resident=True)
+    torch.cuda.synchronize()
+    assert stats["completed"] == stats["offered"] >= 2
+    assert stats["launches"] >= 2   # stopped while idle and launched again
+    _check_held_results(brev_lib, oracle_lib, arena, initial, trace)
+    assert brev_lib.brev_wait_timeouts() == 0
+
+
+def test_resident_server_production_rate(brev_lib, cuda_device):
+    arena = torch.empty(4 << 30, dtype=torch.uint8, device="cuda")
+    stats, _ = brev_lib.brev_server_run_poisson(arena, seed=5, rate_per_s=20000.0, seconds=0.5,
+                                                resident=True)
+    assert stats["completed"] == stats["offered"] > 8000
+    assert 0 < stats["p50_us"] <= stats["p99_us"] <= stats["max_us"]
+    assert stats["host_p50_us"] == stats["p50_us"]
+    assert stats["launches"] == 1
+    assert brev_lib.brev_wait_timeouts() == 0
+    with pytest.raises(brev_lib.BrevError):   # 1- and 2-byte elements: launches only
+        brev_lib.brev_server_run_poisson(arena[: 64 << 20], seed=1, rate_per_s=1000.0,
+                                         seconds=0.01, elem_sizes=(2, 4), resident=True)

@@ -1,0 +1,160 @@
+"""CPU model of the resident serving protocol (host loop, dispatcher warp,
+producer warps, completion words), run over random interleavings with a
+small ring and ticket table so that both wrap around many times.
+
+It follows the kernel and the host loop step by step: the host writes a
+request into ring slot seq % ring with its first ticket and publishes the
+request count; the dispatcher copies requests into the device ring, fills
+the ticket table (ticket % table -> slot) and publishes the ticket count;
+producers claim tickets, wait until they are published (or the run ends),
+look up the slot, and complete units; the units' completions are counted
+per slot and the last one writes seq + 1 into the slot's done word; the
+host admits a request only while its ring slot is free and the tickets
+from the oldest request in flight to the new one fit in the table.
+"""
+import numpy as np
+import pytest
+
+
+def simulate(seed, n_req, ring, table, n_producers, max_slots, restart_every=0):
+    rng = np.random.default_rng(seed)
+    reqs = [(int(rng.integers(1, 7)), int(rng.integers(1, 4))) for _ in range(n_req)]  # units, grain
+    nt_of = [(u + g - 1) // g for u, g in reqs]
+    assert max(nt_of) <= table
+    # shared state
+    h_ring = [None] * ring            # (req index, seq, first ticket)
+    h_done = [0] * ring
+    h_requests = 0
+    h_stop = False
+    d_ring = [None] * ring
+    d_done = [0] * ring
+    d_treq = [None] * table           # (slot, ticket) written for that ticket
+    treq_unread = {}                  # ticket -> still to be read by its producer
+    published = 0
+    ticket_ctr = 0
+    ctl_stop = False
+    unit_runs = {}                    # (req, unit) -> count
+    completed = []
+
+    # host
+    def host():
+        nonlocal h_requests, h_stop
+        next_seq = tickets = 0
+        live = {}                     # seq -> (req, first)
+        nxt = 0
+        while nxt < n_req or live:
+            # completions
+            for seq in list(live):
+                if h_done[seq % ring] == seq + 1:
+                    completed.append(live.pop(seq)[0])
+            # admission of the FIFO head
+            if nxt < n_req and len(live) < max_slots:
+                oldest_seq = min(live) if live else next_seq
+                oldest_t = min(f for _, f in live.values()) if live else tickets
+                nt = nt_of[nxt]
+                if next_seq - oldest_seq < ring and tickets + nt - oldest_t <= table:
+                    h_ring[next_seq % ring] = (nxt, next_seq, tickets)
+                    live[next_seq] = (nxt, tickets)
+                    tickets += nt
+                    next_seq += 1
+                    nxt += 1
+                    h_requests = next_seq          # release store
+            yield
+        h_stop = True
+        yield
+
+    def dispatcher():
+        nonlocal published, ctl_stop
+        seen = 0
+        while True:
+            n = h_requests                           # acquire
+            if n > seen:
+                last = 0
+                for r in range(seen, n):
+                    slot = r % ring
+                    ri, seq, first = h_ring[slot]
+                    assert seq == r
+                    u, g = reqs[ri]
+                    d_ring[slot] = (ri, seq, first, u, g)
+                    d_done[slot] = 0
+                    for t in range(first, first + nt_of[ri]):
+                        old = d_treq[t % table]
+                        if old is not None:
+                            assert not treq_unread.get(old[1], False), "table entry overwritten unread"
+                        d_treq[t % table] = (slot, t)
+                        treq_unread[t] = True
+                    last = first + nt_of[ri]
+                    yield
+                published = last                     # release store
+                seen = n
+            elif h_stop:
+                ctl_stop = True
+                return
+            yield
+
+    def producer():
+        nonlocal ticket_ctr
+        while True:
+            t = ticket_ctr                           # atomicAdd
+            ticket_ctr += 1
+            while True:
+                if published > t:
+                    break
+                if ctl_stop:
+                    if published > t:
+                        break
+                    return
+                yield
+            slot, tt = d_treq[t % table]
+            assert tt == t, "ticket table entry belongs to another ticket"
+            treq_unread[t] = False
+            ri, seq, first, u, g = d_ring[slot]
+            assert first <= t < first + nt_of[ri], "descriptor is not the ticket's request"
+            for unit in range((t - first) * g, min((t - first) * g + g, u)):
+                yield
+                unit_runs[(ri, unit)] = unit_runs.get((ri, unit), 0) + 1
+                d_done[slot] += 1
+                if d_done[slot] == u:
+                    assert h_done[slot] != seq + 1
+                    h_done[slot] = seq + 1
+
+    actors = [host(), dispatcher()] + [producer() for _ in range(n_producers)]
+    live = list(range(len(actors)))
+    steps = 0
+    while live:
+        i = live[int(rng.integers(len(live)))]
+        try:
+            next(actors[i])
+        except StopIteration:
+            live.remove(i)
+        steps += 1
+        assert steps < 2_000_000, "no progress"
+    assert sorted(completed) == list(range(n_req))
+    for ri, (u, g) in enumerate(reqs):
+        for unit in range(u):
+            assert unit_runs.get((ri, unit)) == 1, (ri, unit)
+
+
+@pytest.mark.parametrize("ring,table,max_slots", [(4, 8, 3), (8, 6, 8), (16, 64, 5), (2, 6, 2)])
+def test_resident_protocol(ring, table, max_slots):
+    for seed in range(10):
+        simulate(seed, 60, ring, table, n_producers=5, max_slots=max_slots)
+
+
+def test_resident_protocol_catches_a_short_ticket_window():
+    """Admitting by the sum of in-flight tickets instead of the span from the
+    oldest request in flight would overwrite unread table entries; the model
+    must notice that."""
+    import inspect
+    src = inspect.getsource(simulate).replace(
+        "tickets + nt - oldest_t <= table",
+        "sum(nt_of[r] for r, _ in live.values()) + nt <= table")
+    ns = {"np": np}
+    exec(src, ns)
+    caught = 0
+    for seed in range(20):
+        try:
+            ns["simulate"](seed, 60, 8, 6, n_producers=5, max_slots=8)
+        except AssertionError:
+            caught += 1
+    assert caught > 0
