@@ -371,6 +371,8 @@ def run_brev(args):
         arena = torch.empty(16 << 30, dtype=torch.uint8, device=device)
         native, _ = brev.brev_server_run_poisson(arena, seed=5, rate_per_s=20000.0,
                                                  seconds=args.serve_seconds)
+        resident, _ = brev.brev_server_run_poisson(arena, seed=5, rate_per_s=20000.0,
+                                                   seconds=args.serve_seconds, resident=True)
         del arena
         torch.cuda.empty_cache()
         py = serve_poisson(seconds=min(args.serve_seconds, 5.0), rate=20000.0, seed=5,
@@ -382,6 +384,12 @@ def run_brev(args):
                                "[10,24], E uniform in {4,8,16}, seed 5; arena 16 GiB, 256 "
                                "slots, 4 streams; latency = device completion - arrival")
         serving["clock_sampling"] = "paused (nvidia-smi polling stalls the host loop)"
+        serving["resident"] = {
+            "loop": "one resident kernel fed through a page-locked request ring (no launch "
+                    "per request); latency = completion seen by the serving thread - arrival",
+            **{k: (round(v, 1) if isinstance(v, float) else v) for k, v in resident.items()
+               if k in ("completed", "p50_us", "p99_us", "max_us", "mean_us", "queue_p99_us",
+                        "gbs", "launches", "max_inflight", "peak_pool_bytes")}}
         serving["python_loop"] = {k: py[k] for k in ("completed", "p50_us", "p99_us", "gbs",
                                                      "mean_batch")}
     sampler.stop()

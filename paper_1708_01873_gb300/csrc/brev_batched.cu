@@ -388,12 +388,16 @@ struct ServeDesc {  // device copy of a published request
   int k, E, b, slot;
   unsigned long long seq;
 };
-struct ServeCtl {  // device memory, zeroed before each launch
+struct ServeCtl {  // device memory (256 bytes), zeroed before each launch
+  // the claimed counter (atomics) and the polled words sit on different
+  // 128-byte lines
   unsigned long long ticket;     // next ticket to claim
+  unsigned long long pad0_[15];
   unsigned long long published;  // tickets published by the dispatcher
   int stop;                      // the dispatcher saw the host's stop (or gave up)
-  int pad_;
+  int pad1_;
 };
+static_assert(sizeof(ServeCtl) <= 256, "serving control block");
 struct ServeArgs {
   ServeDesc* d_ring;
   unsigned* d_done;  // per slot: units completed, counted per consumer warp
@@ -407,6 +411,22 @@ struct ServeArgs {
 };
 
 constexpr int SERVE_BLOCK = BATCH_BLOCK + 32;  // consumers, producer, dispatcher
+
+// Ticket sizing of the resident kernel and the producers' longest pause
+// between polls of the published ticket count.
+#ifndef BREV_SERVE_POLL_MAX_NS
+#define BREV_SERVE_POLL_MAX_NS 2048
+#endif
+#ifndef BREV_SERVE_POLL_NS_PER_TICKET
+#define BREV_SERVE_POLL_NS_PER_TICKET 8
+#endif
+#ifndef BREV_SERVE_TICKETS_PER_CTA
+#define BREV_SERVE_TICKETS_PER_CTA 8
+#endif
+#ifndef BREV_SERVE_MAX_TICKET_BYTES
+#define BREV_SERVE_MAX_TICKET_BYTES 65536
+#endif
+
 
 // Dispatcher warp: host ring -> device ring and ticket table.
 __device__ void serve_dispatch(const ServeArgs& A) {
@@ -474,9 +494,9 @@ __device__ __forceinline__ int serve_next_ticket(const ServeArgs& A, BatchDesc& 
   if (lane == 0) {
     t = atomicAdd(&A.ctl->ticket, 1ull);
     const unsigned long long t0 = global_ns();
-    unsigned ns = 32;
     for (;;) {
-      if (ld_acquire_gpu(&A.ctl->published) > t) {
+      const unsigned long long p = ld_acquire_gpu(&A.ctl->published);
+      if (p > t) {
         status = 1;
         break;
       }
@@ -488,8 +508,11 @@ __device__ __forceinline__ int serve_next_ticket(const ServeArgs& A, BatchDesc& 
         status = -1;
         break;
       }
-      __nanosleep(ns);
-      if (ns < 256) ns *= 2;
+      // the holders of the next few tickets poll often, later ones less
+      // (hundreds of producers wait at once; their polls share two L2 lines)
+      const unsigned long long dist = t - p;
+      __nanosleep((unsigned)min(64ull + dist * BREV_SERVE_POLL_NS_PER_TICKET,
+                                (unsigned long long)BREV_SERVE_POLL_MAX_NS));
     }
   }
   status = __shfl_sync(0xffffffffu, status, 0);
@@ -884,9 +907,11 @@ bool resident_shape(int k, int E, int ctas, int* b, unsigned* units, unsigned* g
   *b = bb;
   *units = (unsigned)n_units;
   const unsigned long long max_grain =
-      std::max<unsigned long long>(1, BATCH_TICKET_BYTES / unit_bytes);
+      std::max<unsigned long long>(1, BREV_SERVE_MAX_TICKET_BYTES / unit_bytes);
   *grain = (unsigned)std::min<unsigned long long>(
-      std::max<unsigned long long>(1, n_units / (2ull * (unsigned long long)std::max(ctas, 1))),
+      std::max<unsigned long long>(
+          1, n_units / ((unsigned long long)BREV_SERVE_TICKETS_PER_CTA *
+                        (unsigned long long)std::max(ctas, 1))),
       max_grain);
   return true;
 }
