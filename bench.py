@@ -382,11 +382,13 @@ def run_brev(args):
         serving["loop"] = "native C++ (brev_server_run_poisson)"
         serving["workload"] = ("Poisson arrivals, mean 50 us apart (20k req/s), k uniform in "
                                "[10,24], E uniform in {4,8,16}, seed 5; arena 16 GiB, 256 "
-                               "slots, 4 streams; latency = device completion - arrival")
+                               "slots, 4 streams; latency = completion seen by the serving "
+                               "thread - arrival (device-clock figures: device_p50_us, "
+                               "device_p99_us)")
         serving["clock_sampling"] = "paused (nvidia-smi polling stalls the host loop)"
         serving["resident"] = {
             "loop": "one resident kernel fed through a page-locked request ring (no launch "
-                    "per request); latency = completion seen by the serving thread - arrival",
+                    "per request)",
             **{k: (round(v, 1) if isinstance(v, float) else v) for k, v in resident.items()
                if k in ("completed", "p50_us", "p99_us", "max_us", "mean_us", "queue_p99_us",
                         "gbs", "launches", "max_inflight", "peak_pool_bytes")}}

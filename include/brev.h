@@ -216,8 +216,9 @@ BREV_API brev_status brev_fft_stages(void *dst, const void *src, int log2n, int 
  *     persistent batched kernel for more -- on an idle stream, round robin
  *     over n_streams, so requests arriving while others run overlap with
  *     them on the device.
- *   - Completion: a CUDA event per batch; completion times are read on the
- *     device clock and each request's memory and slot are released.
+ *   - Completion: a CUDA event per batch; when the serving thread sees it
+ *     complete, the batch's requests are complete (latency = that time -
+ *     arrival) and their memory and slots are released.
  * Resident mode (resident = 1) replaces the launches: one kernel stays on
  * the GPU for the whole run and takes requests from a ring in page-locked
  * host memory (NVLink-C2C), so no request pays a kernel launch:
@@ -226,8 +227,7 @@ BREV_API brev_status brev_fft_stages(void *dst, const void *src, int log2n, int 
  *   - each admitted request is written into the ring and published at once;
  *     the kernel spreads its tile units over all CTAs (~64 KiB tickets), so
  *     requests in flight overlap on the device;
- *   - the kernel writes a completion word per request into host memory; its
- *     completion time is when the serving thread sees that word;
+ *   - the kernel writes a completion word per request into host memory;
  *   - element sizes 4, 8 and 16 only (BREV_ERR_UNSUPPORTED otherwise);
  *     max_batch and n_streams are not used.
  *   The kernel's waits are bounded: if the run stalls for 2 s with nothing
@@ -244,23 +244,29 @@ typedef struct brev_server_config {
 } brev_server_config;
 typedef struct brev_server_stats {
     uint64_t offered, completed, batches, launches;
-    double p50_us, p99_us, max_us, mean_us; /* completion - arrival: device clock
-                                             * (launches), serving thread's
-                                             * clock (resident) */
+    double p50_us, p99_us, max_us, mean_us; /* completion seen by the serving
+                                             * thread - arrival (what a client
+                                             * waits), both modes */
     double queue_p99_us;                    /* launch or publication - arrival */
     double req_per_s, gbs, wall_s;          /* gbs: 2 n E bytes per request / wall time */
     uint64_t peak_pool_bytes;
     int max_inflight;
-    double host_p50_us, host_p99_us;        /* completion seen by the serving
-                                             * thread - arrival (both modes) */
+    double device_p50_us, device_p99_us;    /* launches: completion event on the
+                                             * device clock - arrival (read
+                                             * against a reference event, which
+                                             * completed slightly before the run's
+                                             * host clock started, so biased
+                                             * high by that gap); resident:
+                                             * equal to p50_us, p99_us */
 } brev_server_stats;
 typedef struct brev_server_request {
     uint64_t offset; /* byte offset of the request's buffer in the arena */
     int log2n, elem_bytes, batch;
     double arrival_us, launch_us, done_us; /* since the run started; launch: host
                                             * time of the enqueue (publication
-                                            * when resident), done: completion as
-                                            * in p50_us */
+                                            * when resident), done: completion on
+                                            * the device clock (launches) or seen
+                                            * by the serving thread (resident) */
 } brev_server_request;
 
 BREV_API brev_status brev_server_create(const brev_server_config *cfg, void *arena,

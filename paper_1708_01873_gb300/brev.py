@@ -49,7 +49,7 @@ class ServerStats(ctypes.Structure):
                 ("queue_p99_us", ctypes.c_double), ("req_per_s", ctypes.c_double),
                 ("gbs", ctypes.c_double), ("wall_s", ctypes.c_double),
                 ("peak_pool_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_int),
-                ("host_p50_us", ctypes.c_double), ("host_p99_us", ctypes.c_double)]
+                ("device_p50_us", ctypes.c_double), ("device_p99_us", ctypes.c_double)]
 
 
 class ServerRequest(ctypes.Structure):

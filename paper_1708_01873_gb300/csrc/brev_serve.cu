@@ -14,7 +14,8 @@
 //   * a CUDA event per batch marks completion; the request's completion time
 //     is read on the device clock (elapsed time from a reference event
 //     recorded when the run starts) and its memory and slot are released.
-// Latency = device completion time - arrival time.
+// Latency = when the serving thread sees the request complete - arrival
+// time (the device-clock completion time is reported beside it).
 //
 // Resident mode (cfg.resident): the same admission policy, but no launch
 // per request.  One kernel (resident_launch) stays on the GPU for the run;
@@ -152,19 +153,20 @@ void finish_stats(const std::vector<Req>& reqs, const std::vector<double>& lat_u
   out->completed = completed;
   out->batches = batches;
   out->launches = launches;
-  out->p50_us = percentile(lat_us, 50);
-  out->p99_us = percentile(lat_us, 99);
-  out->max_us = lat_us.empty() ? 0 : *std::max_element(lat_us.begin(), lat_us.end());
-  double sum = 0;
-  for (double v : lat_us) sum += v;
-  out->mean_us = lat_us.empty() ? 0 : sum / (double)lat_us.size();
-  out->queue_p99_us = percentile(queue_us, 99);
+  // lat_us: completion on the device clock (launches) or as seen (resident)
   std::vector<double> host_us;
   host_us.reserve(reqs.size());
   for (const Req& r : reqs)
     if (r.seen > 0) host_us.push_back((r.seen - r.arrival) * 1e6);
-  out->host_p50_us = percentile(host_us, 50);
-  out->host_p99_us = percentile(host_us, 99);
+  out->p50_us = percentile(host_us, 50);
+  out->p99_us = percentile(host_us, 99);
+  out->max_us = host_us.empty() ? 0 : *std::max_element(host_us.begin(), host_us.end());
+  double sum = 0;
+  for (double v : host_us) sum += v;
+  out->mean_us = host_us.empty() ? 0 : sum / (double)host_us.size();
+  out->queue_p99_us = percentile(queue_us, 99);
+  out->device_p50_us = percentile(lat_us, 50);
+  out->device_p99_us = percentile(lat_us, 99);
   out->wall_s = wall;
   out->req_per_s = (double)completed / wall;
   out->gbs = (double)bytes_moved / wall / 1e9;
