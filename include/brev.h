@@ -232,7 +232,10 @@ BREV_API brev_status brev_fft_stages(void *dst, const void *src, int log2n, int 
  *     max_batch and n_streams are not used.
  *   The kernel's waits are bounded: if the run stalls for 2 s with nothing
  *   to do (no request and no end of run), it exits, the waits are counted
- *   in brev_wait_timeouts, and the run returns BREV_ERR_CUDA.
+ *   in brev_wait_timeouts, and the run returns BREV_ERR_CUDA.  While it
+ *   runs it holds every SM (other kernels on the device wait); after 0.5 s
+ *   with nothing in flight the host stops it and relaunches it at the next
+ *   request.
  * The arena is a caller-owned device buffer (256-byte aligned); the server
  * owns its streams and events. */
 typedef struct brev_server brev_server;
