@@ -244,6 +244,10 @@ typedef struct brev_server_config {
     int max_batch; /* requests per launch */
     int n_streams; /* streams with a batch in flight, 1..64 */
     int resident;  /* 1: resident kernel fed through host memory, 0: launches */
+    int idle_stop_ms; /* resident: stop the kernel after this long with nothing
+                       * in flight or waiting (0 = 500 ms); above 2000 the
+                       * kernel's own idle limit ends it first, and the run
+                       * fails with BREV_ERR_CUDA at the next request */
 } brev_server_config;
 typedef struct brev_server_stats {
     uint64_t offered, completed, batches, launches;

@@ -38,7 +38,8 @@ class DeviceInfo(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("max_slots", ctypes.c_int), ("max_batch", ctypes.c_int),
-                ("n_streams", ctypes.c_int), ("resident", ctypes.c_int)]
+                ("n_streams", ctypes.c_int), ("resident", ctypes.c_int),
+                ("idle_stop_ms", ctypes.c_int)]
 
 
 class ServerStats(ctypes.Structure):
@@ -336,12 +337,12 @@ def brev_server_run_poisson(arena, seed: int, rate_per_s: float, seconds: float,
                             k_range=(10, 24), elem_sizes=(4, 8, 16), max_slots: int = 256,
                             max_batch: int = 256, n_streams: int = 4,
                             hold_results: bool = False, trace: bool = False,
-                            resident: bool = False):
+                            resident: bool = False, idle_stop_ms: int = 0):
     """Run the native serving loop over the device tensor ``arena`` for a
     seeded Poisson stream; returns (stats dict, trace list or None).
     resident: one kernel fed through page-locked host memory instead of a
     launch per batch."""
-    cfg = ServerConfig(max_slots, max_batch, n_streams, int(bool(resident)))
+    cfg = ServerConfig(max_slots, max_batch, n_streams, int(bool(resident)), idle_stop_ms)
     h = ctypes.c_void_p()
     _check(lib().brev_server_create(ctypes.byref(cfg), arena.data_ptr(),
                                     arena.numel() * arena.element_size(), ctypes.byref(h)),

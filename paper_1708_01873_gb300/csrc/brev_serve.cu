@@ -221,6 +221,8 @@ brev_status run_resident(brev_server* srv, std::vector<Req>& reqs, int hold_resu
   // with sequence numbers and tickets counted from 0.
   bool running = false;
   double last_busy = 0;
+  const double idle_stop =
+      srv->cfg.idle_stop_ms > 0 ? srv->cfg.idle_stop_ms * 1e-3 : kResidentStopIdle;
   auto stop_kernel = [&]() -> cudaError_t {
     __atomic_store_n(&R.h_ctl->stop, 1, __ATOMIC_RELEASE);
     running = false;
@@ -252,7 +254,7 @@ brev_status run_resident(brev_server* srv, std::vector<Req>& reqs, int hold_resu
       live.pop_back();
     }
     if (!live.empty() || !waiting.empty()) last_busy = now;
-    if (running && live.empty() && waiting.empty() && now - last_busy > kResidentStopIdle) {
+    if (running && live.empty() && waiting.empty() && now - last_busy > idle_stop) {
       e = stop_kernel();
       if (e != cudaSuccess) {
         result = cuda_error(e, "resident serving kernel");
@@ -359,7 +361,7 @@ brev_status brev_server_create(const brev_server_config* cfg, void* arena, uint6
   *out = nullptr;
   if (!cfg || cfg->max_slots < 1 || cfg->max_batch < 1 || cfg->n_streams < 1 ||
       cfg->n_streams > 64 || (cfg->resident != 0 && cfg->resident != 1) ||
-      (cfg->resident && cfg->max_slots > (int)kResidentRing))
+      (cfg->resident && cfg->max_slots > (int)kResidentRing) || cfg->idle_stop_ms < 0)
     return set_error(BREV_ERR_INVALID_ARG, "bad server configuration");
   if (!arena || arena_bytes == 0 || (uintptr_t)arena % 256)
     return set_error(BREV_ERR_INVALID_ARG, "arena must be a 256-byte aligned device buffer");

@@ -26,13 +26,14 @@ def _expect(oracle_lib, hosts):
 def test_batched_mixed_vs_oracle(brev_lib, oracle_lib, cuda_device):
     rng = np.random.default_rng(11)
     arrays, hosts = _make_batch(rng, 300, list(range(0, 19)), [4, 8, 16], 100)
+    t0 = brev_lib.brev_wait_timeouts()
     c0 = brev_lib.brev_launch_count()
     brev_lib.brev_permute_batched(arrays)
     torch.cuda.synchronize()
     assert brev_lib.brev_launch_count() - c0 == 1  # one persistent launch
     for a, e, (k, E, _) in zip(arrays, _expect(oracle_lib, hosts), hosts):
         assert_bytes_equal(to_bytes(a), e, E, f"batched k={k} E={E}")
-    assert brev_lib.brev_wait_timeouts() == 0  # no CTA gave up on its copies
+    assert brev_lib.brev_wait_timeouts() == t0  # no CTA gave up on its copies
 
 
 def test_batched_single_elem_size_api(brev_lib, oracle_lib, cuda_device):
@@ -136,6 +137,7 @@ def test_batched_config4_full_size(brev_lib, oracle_lib, cuda_device):
         a = torch.empty((1 << k) * E, dtype=torch.uint8, device="cuda")
         inputs.fill_torch(a, 40000 + i, KIND[E], chunk=1 << 26)
         arrays.append(a.view(DTYPE[E]))
+    t0 = brev_lib.brev_wait_timeouts()
     plan = brev_lib.BrevPlan(arrays)
     plan.launch()
     torch.cuda.synchronize()
@@ -161,7 +163,7 @@ def test_batched_config4_full_size(brev_lib, oracle_lib, cuda_device):
         inputs.fill_torch(ref, 40000 + i, KIND[E], chunk=1 << 26)
         assert torch.equal(arrays[i].view(torch.uint8), ref), f"array {i} after two replays"
     plan.close()
-    assert brev_lib.brev_wait_timeouts() == 0
+    assert brev_lib.brev_wait_timeouts() == t0
 
 
 def test_host_path(brev_lib, oracle_lib, cuda_device):

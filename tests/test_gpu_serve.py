@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 import torch
 
-from gpu_util import DTYPE, KIND, assert_bytes_equal
+from gpu_util import DTYPE, KIND, assert_bytes_equal, device_array, host_array, to_bytes
 from paper_1708_01873_gb300 import inputs
 from paper_1708_01873_gb300.serve import GpuBackend, Server, poisson_requests
 
@@ -126,6 +126,7 @@ def test_resident_server_results_equal_alone(brev_lib, oracle_lib, cuda_device):
     stream (requests overlapping on the device); with results held, every
     request's region equals the single-array permutation of its initial
     bytes, and the oracle for the small ones."""
+    t0 = brev_lib.brev_wait_timeouts()
     arena = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     inputs.fill_torch(arena, 98, "u8", chunk=1 << 26)
     initial = arena.clone()
@@ -139,12 +140,13 @@ def test_resident_server_results_equal_alone(brev_lib, oracle_lib, cuda_device):
     spans = sorted((r["offset"], r["offset"] + (r["elem_bytes"] << r["log2n"])) for r in trace)
     assert all(a[1] <= b[0] for a, b in zip(spans, spans[1:]))
     _check_held_results(brev_lib, oracle_lib, arena, initial, trace)
-    assert brev_lib.brev_wait_timeouts() == 0
+    assert brev_lib.brev_wait_timeouts() == t0
 
 
 def test_resident_server_restarts_after_idle(brev_lib, oracle_lib, cuda_device):
     """Arrivals further apart than the idle limit: the host stops the kernel
     between them and launches it again; every result is still right."""
+    t0 = brev_lib.brev_wait_timeouts()
     arena = torch.empty(64 << 20, dtype=torch.uint8, device="cuda")
     inputs.fill_torch(arena, 97, "u8", chunk=1 << 26)
     initial = arena.clone()
@@ -156,10 +158,11 @@ def test_resident_server_restarts_after_idle(brev_lib, oracle_lib, cuda_device):
     assert stats["completed"] == stats["offered"] >= 2
     assert stats["launches"] >= 2   # stopped while idle and launched again
     _check_held_results(brev_lib, oracle_lib, arena, initial, trace)
-    assert brev_lib.brev_wait_timeouts() == 0
+    assert brev_lib.brev_wait_timeouts() == t0
 
 
 def test_resident_server_production_rate(brev_lib, cuda_device):
+    t0 = brev_lib.brev_wait_timeouts()
     arena = torch.empty(4 << 30, dtype=torch.uint8, device="cuda")
     stats, _ = brev_lib.brev_server_run_poisson(arena, seed=5, rate_per_s=20000.0, seconds=0.5,
                                                 resident=True)
@@ -167,7 +170,57 @@ def test_resident_server_production_rate(brev_lib, cuda_device):
     assert 0 < stats["p50_us"] <= stats["p99_us"] <= stats["max_us"]
     assert stats["device_p50_us"] == stats["p50_us"]
     assert stats["launches"] == 1
-    assert brev_lib.brev_wait_timeouts() == 0
+    assert brev_lib.brev_wait_timeouts() == t0
+    with pytest.raises(brev_lib.BrevError):   # more slots than the request ring
+        brev_lib.brev_server_run_poisson(arena[: 64 << 20], seed=1, rate_per_s=1000.0,
+                                         seconds=0.01, max_slots=5000, resident=True)
     with pytest.raises(brev_lib.BrevError):   # 1- and 2-byte elements: launches only
         brev_lib.brev_server_run_poisson(arena[: 64 << 20], seed=1, rate_per_s=1000.0,
                                          seconds=0.01, elem_sizes=(2, 4), resident=True)
+
+
+def _arrivals(seed, rate, seconds):
+    """The server's seeded arrival times (SplitMix64, exponential gaps), as
+    brev_server_run_poisson draws them."""
+    import math
+    M = (1 << 64) - 1
+    state = [seed & M]
+
+    def sm64():
+        state[0] = (state[0] + 0x9E3779B97F4A7C15) & M
+        z = state[0]
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M
+        return z ^ (z >> 31)
+
+    t, out = 0.0, []
+    while True:
+        t += -math.log(((sm64() >> 11) + 1) * (1.0 / 9007199254740992.0)) / rate
+        if t >= seconds:
+            return out
+        out.append(t)
+        sm64()
+        sm64()   # k and E draws
+
+
+def test_resident_kernel_idle_limit_is_reported(brev_lib, oracle_lib, cuda_device):
+    """Failure detection without a fault: with the host's idle stop disabled
+    (20 s) and a 3 s gap between two requests, the kernel's own 2 s idle
+    limit ends it; the next request finds no kernel, the run returns
+    BREV_ERR_CUDA, the wait timeout is counted, and the device keeps
+    working."""
+    seed = next(s for s in range(200)
+                if len(a := _arrivals(s, 0.5, 6.0)) >= 2 and a[0] < 1.5 and a[1] - a[0] > 3.0)
+    arena = torch.empty(64 << 20, dtype=torch.uint8, device="cuda")
+    before = brev_lib.brev_wait_timeouts()
+    with pytest.raises(brev_lib.BrevError) as err:
+        brev_lib.brev_server_run_poisson(arena, seed=seed, rate_per_s=0.5, seconds=6.0,
+                                         k_range=(10, 12), elem_sizes=(8,), resident=True,
+                                         idle_stop_ms=20000)
+    assert err.value.status == 5   # BREV_ERR_CUDA
+    assert brev_lib.brev_wait_timeouts() > before
+    x = device_array(77, 14, 16)
+    y = torch.empty_like(x)
+    brev_lib.brev_permute_to(y, x)
+    assert_bytes_equal(to_bytes(y), oracle_lib.brev_oop(host_array(77, 14, 16), 14, 16), 16,
+                       "after the timeout")
