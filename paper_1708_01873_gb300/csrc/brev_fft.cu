@@ -20,6 +20,9 @@
 
 namespace brev {
 
+#ifndef BREV_FFT_IP_THREADS_MULT
+#define BREV_FFT_IP_THREADS_MULT 1  // in-place CTA threads vs the out-of-place CTA (x2 spilled)
+#endif
 #ifndef BREV_FFT_MIN_CTAS
 #define BREV_FFT_MIN_CTAS 5  // register budget for 5 resident CTAs per SM (measured best)
 #endif
@@ -88,12 +91,14 @@ __device__ __forceinline__ T twiddle_const(T b, int inverse, const T* tw, int sh
 // Stages 1..R (R <= 3) of every output row, in registers, with the
 // twiddles resolved at compile time (groups are 2^R consecutive elements).
 template <class G, int NTHR, int R>
-__device__ __forceinline__ void dit_first_pass(uint4* sm, int inverse,
+__device__ __forceinline__ void dit_first_pass(uint4* sm0, int nt, int inverse,
                                                const typename Cplx<G::E>::T* tw) {
   using T = typename Cplx<G::E>::T;
   constexpr int GN = 1 << R;
-  const int groups = 1 << (G::BX + G::BZ - R);
-  for (int g = threadIdx.x; g < groups; g += NTHR) {
+  constexpr int LOG_GROUPS = G::BX + G::BZ - R;  // groups per tile
+  for (int gt = threadIdx.x; gt < (nt << LOG_GROUPS); gt += NTHR) {
+    uint4* sm = sm0 + (gt >> LOG_GROUPS) * G::CHUNKS;  // the nt staged tiles, one after another
+    const int g = gt & ((1 << LOG_GROUPS) - 1);
     const int z = g & ((1 << G::BZ) - 1);
     const int base = (g >> G::BZ) << R;
     T v[GN];
@@ -136,12 +141,14 @@ __device__ __forceinline__ void dit_first_pass(uint4* sm, int inverse,
 // column, X = base + j + t 2^s0 (t < 2^R), which those R stages combine only
 // among themselves (the radix-2^R view of R consecutive radix-2 stages).
 template <class G, int NTHR, int R>
-__device__ __forceinline__ void dit_pass(uint4* sm, int s0, int inverse,
+__device__ __forceinline__ void dit_pass(uint4* sm0, int nt, int s0, int inverse,
                                          const typename Cplx<G::E>::T* tw) {
   using T = typename Cplx<G::E>::T;
   constexpr int GN = 1 << R;
-  const int groups = 1 << (G::BX + G::BZ - R);
-  for (int g = threadIdx.x; g < groups; g += NTHR) {
+  constexpr int LOG_GROUPS = G::BX + G::BZ - R;
+  for (int gt = threadIdx.x; gt < (nt << LOG_GROUPS); gt += NTHR) {
+    uint4* sm = sm0 + (gt >> LOG_GROUPS) * G::CHUNKS;
+    const int g = gt & ((1 << LOG_GROUPS) - 1);
     const int z = g & ((1 << G::BZ) - 1);
     const int q = g >> G::BZ;
     const int j = q & ((1 << s0) - 1);
@@ -171,20 +178,20 @@ __device__ __forceinline__ void dit_pass(uint4* sm, int s0, int inverse,
 // at a time: the first pass with compile-time twiddles, later ones from the
 // table.
 template <class G, int NTHR>
-__device__ __forceinline__ void dit_stages(uint4* sm, int S, int inverse,
+__device__ __forceinline__ void dit_stages(uint4* sm, int nt, int S, int inverse,
                                            const typename Cplx<G::E>::T* tw) {
   if (S <= 0) return;
   const int R0 = S >= 3 ? 3 : S;
-  if (R0 == 3) dit_first_pass<G, NTHR, 3>(sm, inverse, tw);
-  else if (R0 == 2) dit_first_pass<G, NTHR, 2>(sm, inverse, tw);
-  else dit_first_pass<G, NTHR, 1>(sm, inverse, tw);
+  if (R0 == 3) dit_first_pass<G, NTHR, 3>(sm, nt, inverse, tw);
+  else if (R0 == 2) dit_first_pass<G, NTHR, 2>(sm, nt, inverse, tw);
+  else dit_first_pass<G, NTHR, 1>(sm, nt, inverse, tw);
   __syncthreads();
   int s0 = R0;
   while (s0 < S) {
     const int R = S - s0 >= 3 ? 3 : S - s0;
-    if (R == 3) dit_pass<G, NTHR, 3>(sm, s0, inverse, tw);
-    else if (R == 2) dit_pass<G, NTHR, 2>(sm, s0, inverse, tw);
-    else dit_pass<G, NTHR, 1>(sm, s0, inverse, tw);
+    if (R == 3) dit_pass<G, NTHR, 3>(sm, nt, s0, inverse, tw);
+    else if (R == 2) dit_pass<G, NTHR, 2>(sm, nt, s0, inverse, tw);
+    else dit_pass<G, NTHR, 1>(sm, nt, s0, inverse, tw);
     s0 += R;
     __syncthreads();
   }
@@ -207,14 +214,33 @@ __global__ void __launch_bounds__(Geom<E, 16, B, B>::THREADS, BREV_FFT_MIN_CTAS)
   const uint64_t stride = (uint64_t)E << (k - B);
   load_tiles<G, true, G::THREADS, 1>(smem_u4, src + ((uint64_t)y << B) * E, nullptr, stride, 1);
   __syncthreads();
-  dit_stages<G, G::THREADS>(smem_u4, S, inverse, tw);
+  dit_stages<G, G::THREADS>(smem_u4, 1, S, inverse, tw);
   store_tile<G, G::THREADS>(smem_u4, dst + ((uint64_t)ry << B) * E, stride);
 }
 
+// In place: NTHR threads; each FFT pass takes the groups of both staged
+// tiles of the pair at once (one barrier per pass for the pair).
 template <int E, int B>
-__global__ void __launch_bounds__(Geom<E, 16, B, B>::THREADS, BREV_FFT_MIN_CTAS)
+__host__ __device__ constexpr int fft_ip_threads() {
+  return Geom<E, 16, B, B>::THREADS * BREV_FFT_IP_THREADS_MULT > 1024
+             ? 1024
+             : Geom<E, 16, B, B>::THREADS * BREV_FFT_IP_THREADS_MULT;
+}
+
+// In-place register budget: complex<float> pairs of 2^6 x 2^6 tiles fill
+// shared memory at 3 CTAs per SM, and a budget for 3 beats one for 5
+// (0.845 vs 0.879 ms, 6 stages, k = 28); complex<double> is FP64-bound and
+// keeps the 5-CTA budget (8.53 vs 8.64 ms).
+template <int E>
+__host__ __device__ constexpr int fft_ip_min_ctas() {
+  return E == 8 ? 3 : BREV_FFT_MIN_CTAS;
+}
+
+template <int E, int B>
+__global__ void __launch_bounds__(fft_ip_threads<E, B>(), fft_ip_min_ctas<E>())
     k_fft_inplace(char* data, int k, int S, int inverse) {
   using G = Geom<E, 16, B, B>;
+  constexpr int NTHR = fft_ip_threads<E, B>();
   using T = typename Cplx<E>::T;
   extern __shared__ uint4 smem_u4[];
   T* tw = reinterpret_cast<T*>(smem_u4 + 2 * G::CHUNKS);
@@ -238,12 +264,11 @@ __global__ void __launch_bounds__(Geom<E, 16, B, B>::THREADS, BREV_FFT_MIN_CTAS)
   const uint64_t stride = (uint64_t)E << (k - B);
   char* const ty = data + ((uint64_t)y << B) * E;
   char* const tr = data + ((uint64_t)ry << B) * E;
-  load_tiles<G, false, G::THREADS, 2>(smem_u4, ty, tr, stride, nt);
+  load_tiles<G, false, NTHR, 2>(smem_u4, ty, tr, stride, nt);
   __syncthreads();
-  dit_stages<G, G::THREADS>(smem_u4, S, inverse, tw);
-  if (nt == 2) dit_stages<G, G::THREADS>(smem_u4 + G::CHUNKS, S, inverse, tw);
-  store_tile<G, G::THREADS>(smem_u4, tr, stride);
-  if (nt == 2) store_tile<G, G::THREADS>(smem_u4 + G::CHUNKS, ty, stride);
+  dit_stages<G, NTHR>(smem_u4, nt, S, inverse, tw);  // both tiles in each pass
+  store_tile<G, NTHR>(smem_u4, tr, stride);
+  if (nt == 2) store_tile<G, NTHR>(smem_u4 + G::CHUNKS, ty, stride);
 }
 
 // Small arrays (and any array that fits): one CTA stages the permuted array
@@ -289,7 +314,7 @@ __global__ void __launch_bounds__(256) k_fft_small(char* dst, const char* src, i
 struct FftKernel {
   const void* oop;
   const void* inplace;
-  int B, threads;
+  int B, threads, ip_threads;
   unsigned tile_bytes;
 };
 
@@ -297,7 +322,7 @@ template <int E, int B>
 static FftKernel fft_k() {
   using G = Geom<E, 16, B, B>;
   return {(const void*)&k_fft_oop<E, B>, (const void*)&k_fft_inplace<E, B>, B, G::THREADS,
-          G::TILE_BYTES};
+          fft_ip_threads<E, B>(), G::TILE_BYTES};
 }
 
 static bool fft_lookup(int E, int B, FftKernel* out) {
@@ -373,7 +398,7 @@ extern "C" brev_status brev_fft_stages(void* dst, const void* src, int log2n, in
     if (e != cudaSuccess) return cuda_error(e, "shared-memory limit");
     char* d = (char*)dst;
     void* args[] = {(void*)&d, (void*)&kk, (void*)&SS, (void*)&inv};
-    e = launch_pdl(K.inplace, (unsigned)grid, K.threads, args, smem, s);
+    e = launch_pdl(K.inplace, (unsigned)grid, K.ip_threads, args, smem, s);
   } else {
     const unsigned long long grid = 1ull << (k - 2 * K.B);
     const unsigned smem = K.tile_bytes + tw_bytes;

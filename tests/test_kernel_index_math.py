@@ -789,6 +789,25 @@ def test_fused_fft_register_passes():
             assert np.allclose(got, exp, atol=1e-12), (B, S)
 
 
+def test_fused_fft_pair_passes_cover_both_tiles():
+    """In place, one pass loop runs the groups of both staged tiles of a
+    pair: index gt -> tile gt >> LOG_GROUPS (at gt's tile offset), group
+    gt & (groups - 1); each (tile, group) exactly once for any thread count."""
+    for B in (3, 4, 5, 6):
+        for R in (1, 2, 3):
+            log_groups = 2 * B - R
+            for nt in (1, 2):
+                for nthr in (64, 256, 512):
+                    seen = set()
+                    for tid in range(nthr):
+                        for gt in range(tid, nt << log_groups, nthr):
+                            tile, g = gt >> log_groups, gt & ((1 << log_groups) - 1)
+                            assert 0 <= tile < nt
+                            assert (tile, g) not in seen
+                            seen.add((tile, g))
+                    assert len(seen) == nt << log_groups
+
+
 class _MBar:
     """mbarrier phase semantics: a phase completes when its pending
     arrivals reach 0 and its transaction bytes are all in; try_wait(P) is
