@@ -331,6 +331,14 @@ brev_status launch_single(void* dst, const void* src, int k, int E, cudaStream_t
   return launch_choice(choose(k, E, inplace, vec16), dst, src, k, E, stream);
 }
 
+void preload_single(int k, int E, bool inplace) {
+  if (!valid_E(E) || k < 0 || k > BREV_MAX_LOG2N || (inplace && k <= 1)) return;
+  const Choice c = choose(k, E, inplace, true);
+  const void* kern = c.small ? small_kernel(E) : (c.entry ? c.entry->kernel : nullptr);
+  cudaFuncAttributes fa;
+  if (kern && cudaFuncGetAttributes(&fa, kern) != cudaSuccess) cudaGetLastError();
+}
+
 static brev_status check_common(int k, int E) {
   if (!valid_E(E))
     return set_error(BREV_ERR_INVALID_ARG, "elem_bytes=%d (must be 1, 2, 4, 8 or 16)", E);

@@ -806,6 +806,11 @@ static brev_status enqueue_batch(const BatchPlanData& p, const BatchDesc* d_desc
   return BREV_OK;
 }
 
+void preload_batched() {
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, (const void*)k_batched) != cudaSuccess) cudaGetLastError();
+}
+
 brev_status batched_launch(const BatchItem* items, int count, cudaStream_t stream) {
   return batched_launch_forced(items, count, -1, stream);
 }
@@ -835,6 +840,26 @@ brev_status batched_launch_forced(const BatchItem* items, int count, int b,
   s = enqueue_batch(p, (const BatchDesc*)ws, d_ticket, stream);
   cudaFreeAsync(ws, stream);
   return s;
+}
+
+size_t batched_ws_bytes(int count) {
+  return ((size_t)std::max(count, 0) * sizeof(BatchDesc) + 15) / 16 * 16 + 64;
+}
+
+brev_status batched_launch_into(const BatchItem* items, int count, void* ws, size_t ws_bytes,
+                                cudaStream_t stream) {
+  BatchPlanData p;
+  brev_status s = build_batch(items, count, &p);
+  if (s != BREV_OK) return s;
+  if (p.desc.empty()) return enqueue_batch(p, nullptr, nullptr, stream);
+  const size_t desc_bytes = p.desc.size() * sizeof(BatchDesc);
+  if (!ws || batched_ws_bytes((int)p.desc.size()) > ws_bytes)
+    return set_error(BREV_ERR_INVALID_ARG, "batched workspace too small");
+  // pageable source: staged before the call returns
+  cudaError_t e = cudaMemcpyAsync(ws, p.desc.data(), desc_bytes, cudaMemcpyHostToDevice, stream);
+  if (e != cudaSuccess) return cuda_error(e, "descriptor upload");
+  auto* d_ticket = reinterpret_cast<unsigned long long*>((char*)ws + ((desc_bytes + 15) / 16) * 16);
+  return enqueue_batch(p, (const BatchDesc*)ws, d_ticket, stream);
 }
 
 int transpose_pipelined_b(int E) {

@@ -65,6 +65,12 @@ struct BatchItem {
   int E;
 };
 brev_status batched_launch(const BatchItem* items, int count, cudaStream_t stream);
+// The same launch with a caller-owned device workspace of ws_bytes >=
+// batched_ws_bytes(count) (free for reuse once the stream has passed the
+// launch); allocates nothing.
+size_t batched_ws_bytes(int count);
+brev_status batched_launch_into(const BatchItem* items, int count, void* ws, size_t ws_bytes,
+                                cudaStream_t stream);
 // The same launch with tile exponent `b` forced for every array (the
 // tuner's candidates; each array must accept b, see batched_candidates).
 brev_status batched_launch_forced(const BatchItem* items, int count, int b,
@@ -124,5 +130,10 @@ int tuned_batched_b(int k, int E);
 brev_status validate_batch_items(const BatchItem* items, int count);
 // Launch one permutation without argument checks (src == dst: in-place).
 brev_status launch_single(void* dst, const void* src, int k, int E, cudaStream_t stream);
+// Load the kernel that launch_single would use for (k, E, in place) -- with
+// lazy module loading a kernel is otherwise loaded at its first launch.
+void preload_single(int k, int E, bool inplace);
+// The same for the batched kernel.
+void preload_batched();
 
 }  // namespace brev
