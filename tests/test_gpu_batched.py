@@ -166,6 +166,31 @@ def test_batched_config4_full_size(brev_lib, oracle_lib, cuda_device):
     assert brev_lib.brev_wait_timeouts() == t0
 
 
+def test_batched_with_a_16gib_array(brev_lib, cuda_device):
+    """A batch holding one 2^32-element float32 array (16 GiB, indices past
+    2^32) and small ones: each array equals its single-array permutation, and
+    a second launch restores the inputs."""
+    t0 = brev_lib.brev_wait_timeouts()
+    big = device_array(4321, 32, 4)
+    small = [device_array(4400 + i, k, E) for i, (k, E) in enumerate(((9, 8), (14, 16), (20, 4)))]
+    arrays = [big] + small
+    refs = []
+    for a in arrays:
+        r = a.clone()
+        brev_lib.brev_permute(r, in_place=True)
+        refs.append(r)
+    torch.cuda.synchronize()
+    brev_lib.brev_permute_batched(arrays)
+    torch.cuda.synchronize()
+    for a, r in zip(arrays, refs):
+        assert torch.equal(a.view(torch.uint8), r.view(torch.uint8))
+    del refs
+    brev_lib.brev_permute_batched(arrays)
+    torch.cuda.synchronize()
+    assert torch.equal(big.view(torch.uint8), device_array(4321, 32, 4).view(torch.uint8))
+    assert brev_lib.brev_wait_timeouts() == t0
+
+
 def test_host_path(brev_lib, oracle_lib, cuda_device):
     for k, E in ((0, 16), (7, 4), (20, 16), (23, 8)):
         hb = host_array(70 + k, k, E)

@@ -153,6 +153,10 @@ def _check_sampled(oracle_lib, out: torch.Tensor, seed: int, k: int, E: int, kin
     (29, 8, "c64", False),     # 4 GiB complex<float>, odd k, out of place
     (26, 16, "c128", False),
     (27, 4, "u32", False),
+    # beyond 2^32 elements / bytes: 64-bit index arithmetic (16 GiB arrays)
+    (32, 4, "u32", True),
+    (33, 2, "u16", True),
+    (34, 1, "u8", False),      # the largest log2n the API accepts
 ])
 def test_full_size_sampled(brev_lib, oracle_lib, cuda_device, k, E, kind, inplace):
     rng = np.random.default_rng(k * 100 + E)
