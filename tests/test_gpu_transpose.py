@@ -128,6 +128,23 @@ def test_transpose_in_place_full_size_equals_out_of_place(brev_lib, cuda_device)
     assert brev_lib.brev_wait_timeouts() == t0
 
 
+def test_transpose_past_2_to_32_elements(brev_lib, cuda_device):
+    """65536 x 65536 uint32 (16 GiB, indices past 2^32): in place equals
+    out of place, and transposing back restores the input."""
+    t0 = brev_lib.brev_wait_timeouts()
+    a, E = 16, 4
+    src = device_array(991, 2 * a, E)
+    ref = torch.empty_like(src)
+    brev_lib.brev_transpose(ref, src, a, a)
+    buf = src.clone()
+    brev_lib.brev_transpose(buf, buf, a, a)
+    assert torch.equal(buf.view(torch.uint8), ref.view(torch.uint8))
+    del ref
+    brev_lib.brev_transpose(buf, buf, a, a)
+    assert torch.equal(buf.view(torch.uint8), src.view(torch.uint8))
+    assert brev_lib.brev_wait_timeouts() == t0
+
+
 def test_transpose_in_place_captured_in_graph(brev_lib, oracle_lib, cuda_device):
     """The in-place transposition enqueues only capturable work (a
     stream-ordered allocation, a memset and the kernel): capture it once,
