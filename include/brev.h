@@ -315,10 +315,12 @@ BREV_API brev_status brev_permute_host(void *dst_host, const void *src_host, int
 /* Tile shape used for (log2n, elem_bytes, in_place): bx high bits and bz
  * low bits per tile (the matrix-buffer side lengths 2^bx, 2^bz); bx = bz =
  * 0 means the whole array is staged in one CTA (small arrays).  order is
- * the launch order of the tiles: 0 = tile y run by CTA y, 1 = blocked
- * (consecutive CTAs take 8 x 8 blocks of (high, low) bits of y, so that
- * both the tiles and their destinations come in runs of 8 adjacent tiles).
- * Host-only query, no GPU needed. */
+ * how the tiles are run: 0 = tile y by CTA y, 1 = blocked (consecutive
+ * CTAs take 8 x 8 blocks of (high, low) bits of y, so that both the tiles
+ * and their destinations come in runs of 8 adjacent tiles), 2 = the TMA
+ * pipeline (in place only: persistent CTAs take tickets of tile pairs and
+ * stage their rows by bulk copies; element sizes 4, 8, 16).  Host-only
+ * query, no GPU needed. */
 BREV_API brev_status brev_tile_shape(int log2n, int elem_bytes, int in_place, int *bx, int *bz,
                                      int *order);
 
@@ -340,14 +342,16 @@ BREV_API brev_status brev_permute_shape(void *dst, const void *src, int log2n, i
                                         int bx, int bz, int order, void *stream);
 
 /* Number of compiled 16-byte-path (tile shape, launch order) pairs for
- * (elem_bytes, in_place), and the i-th one (host-only; the tuner's
- * candidates). */
+ * (elem_bytes, in_place), including the TMA pipeline's tile exponents (order
+ * 2) for in place, and the i-th one (host-only; the tuner's candidates). */
 BREV_API int brev_shape_count(int elem_bytes, int in_place);
 BREV_API brev_status brev_shape_at(int elem_bytes, int in_place, int i, int *bx, int *bz,
                                    int *order);
 
 /* Time every compiled shape for k in [k_min, k_max] (out-of-place and
- * in-place), keep the fastest in the library's table, and, if cache_path
+ * in-place; in place also the TMA pipeline, order 2, so the choice between
+ * the LSU tile kernels and bulk-copy staging is measured per (k, E)), keep
+ * the fastest in the library's table, and, if cache_path
  * is not NULL, write the table as JSON.  For elem_bytes 4, 8 and 16 it also
  * times the batched kernel's tile exponent b for each k up to 24 on a
  * batch of equal arrays (up to 4096 arrays, about 256 MiB), and keeps the

@@ -239,6 +239,7 @@ int tuned_batched_b(int k, int E) {
 struct Choice {
   bool small;
   const ShapeEntry* entry;
+  int pipe_b = 0;  // > 0: in place on the TMA pipeline with 2^b x 2^b tiles (order 2)
 };
 
 static Choice choose_default(int k, int E, bool inplace, bool vec16);
@@ -250,6 +251,8 @@ static Choice choose(int k, int E, bool inplace, bool vec16) {
   if (vec16) {
     std::lock_guard<std::mutex> lk(g_mu);
     const int8_t* t = g_tuned[e_index(E)][kind][k];
+    if (t[2] == 2 && inplace && t[0] == t[1] && pipeline_shape_ok(k, E, t[0]))
+      return {false, nullptr, t[0]};
     if (t[0] > 0 && t[1] > 0 && t[0] + t[1] <= k)
       if (const ShapeEntry* s = find_shape(E, 16, t[0], t[1], kind, t[2])) return {false, s};
   }
@@ -290,6 +293,7 @@ cudaError_t launch_pdl(const void* kern, unsigned grid, unsigned threads, void**
 
 static brev_status launch_choice(const Choice& c, void* dst, const void* src, int k, int E,
                                  cudaStream_t stream) {
+  if (c.pipe_b > 0) return bitrev_inplace_pipelined(dst, k, E, c.pipe_b, stream);
   cudaError_t e;
   if (c.small) {
     const void* kern = small_kernel(E);
@@ -334,6 +338,10 @@ brev_status launch_single(void* dst, const void* src, int k, int E, cudaStream_t
 void preload_single(int k, int E, bool inplace) {
   if (!valid_E(E) || k < 0 || k > BREV_MAX_LOG2N || (inplace && k <= 1)) return;
   const Choice c = choose(k, E, inplace, true);
+  if (c.pipe_b > 0) {
+    preload_batched();
+    return;
+  }
   const void* kern = c.small ? small_kernel(E) : (c.entry ? c.entry->kernel : nullptr);
   cudaFuncAttributes fa;
   if (kern && cudaFuncGetAttributes(&fa, kern) != cudaSuccess) cudaGetLastError();
@@ -428,7 +436,16 @@ brev_status brev_permute_shape(void* dst, const void* src, int log2n, int elem_b
       return set_error(BREV_ERR_INVALID_ARG, "tile %dx%d does not fit k=%d", bx, bz, log2n);
     if (inplace && bx != bz)
       return set_error(BREV_ERR_INVALID_ARG, "in-place needs a square tile");
-    if (order != 0 && order != 1) return set_error(BREV_ERR_INVALID_ARG, "order=%d", order);
+    if (order < 0 || order > 2) return set_error(BREV_ERR_INVALID_ARG, "order=%d", order);
+    if (order == 2) {  // the TMA pipeline: in place, 16-byte aligned
+      if (!inplace || !vec16 || !pipeline_shape_ok(log2n, elem_bytes, bx))
+        return set_error(BREV_ERR_UNSUPPORTED,
+                         "order 2 (TMA pipeline) needs in place, 16-byte alignment and a "
+                         "pipeline tile (k=%d E=%d b=%d)",
+                         log2n, elem_bytes, bx);
+      return launch_choice(Choice{false, nullptr, bx}, dst, src, log2n, elem_bytes,
+                           (cudaStream_t)stream);
+    }
     c.entry = find_shape(elem_bytes, vec16 ? 16 : elem_bytes, bx, bz, inplace ? 1 : 0, order);
     if (!c.entry)
       return set_error(BREV_ERR_UNSUPPORTED, "tile %dx%d order %d not compiled for E=%d (%s path)",
@@ -525,6 +542,11 @@ brev_status brev_tile_shape(int log2n, int elem_bytes, int in_place, int* bx, in
     *bx = *bz = *order = 0;
     return BREV_OK;
   }
+  if (c.pipe_b > 0) {
+    *bx = *bz = c.pipe_b;
+    *order = 2;
+    return BREV_OK;
+  }
   if (!c.entry) return set_error(BREV_ERR_UNSUPPORTED, "no tile shape");
   *bx = c.entry->bx;
   *bz = c.entry->bz;
@@ -538,6 +560,8 @@ int brev_shape_count(int elem_bytes, int in_place) {
   const int kind = in_place ? 1 : 0;
   for (int i = 0; i < n; ++i)
     if (t[i].E == elem_bytes && t[i].W == 16 && t[i].kind == kind) ++c;
+  int pb[8];
+  if (in_place) c += pipeline_shapes(elem_bytes, pb);  // order 2 (TMA pipeline)
   return c;
 }
 
@@ -556,6 +580,13 @@ brev_status brev_shape_at(int elem_bytes, int in_place, int i, int* bx, int* bz,
       }
       ++c;
     }
+  int pb[8];
+  const int np = in_place ? pipeline_shapes(elem_bytes, pb) : 0;
+  if (i >= c && i < c + np) {
+    *bx = *bz = pb[i - c];
+    *order = 2;
+    return BREV_OK;
+  }
   return set_error(BREV_ERR_INVALID_ARG, "shape index %d out of range", i);
 }
 
@@ -685,8 +716,9 @@ brev_status brev_load_tune_cache(const char* path) {
         json_int(p, q, "in_place", &ip) && json_int(p, q, "bx", &bx) &&
         json_int(p, q, "bz", &bz) && valid_E((int)E) && k >= 0 && k <= BREV_MAX_LOG2N &&
         (ip == 0 || ip == 1) && bx > 0 && bz > 0 && bx + bz <= k && (ip == 0 || bx == bz) &&
-        (order == 0 || order == 1) &&
-        find_shape((int)E, 16, (int)bx, (int)bz, (int)ip, (int)order)) {
+        (((order == 0 || order == 1) &&
+          find_shape((int)E, 16, (int)bx, (int)bz, (int)ip, (int)order)) ||
+         (order == 2 && ip == 1 && pipeline_shape_ok((int)k, (int)E, (int)bx)))) {
       int8_t* t = g_tuned[e_index((int)E)][ip][k];
       t[0] = (int8_t)bx;
       t[1] = (int8_t)bz;
@@ -831,6 +863,36 @@ brev_status brev_autotune(int k_min, int k_max, int elem_bytes, const char* cach
             bord = t[i].order;
           }
         }
+        // in place: the TMA pipeline (order 2) for each of its tile exponents
+        int pb[8];
+        const int np = (ip && result == BREV_OK) ? pipeline_shapes(E, pb) : 0;
+        for (int i = 0; i < np && result == BREV_OK; ++i) {
+          if (!pipeline_shape_ok(k, E, pb[i])) continue;
+          Choice c{false, nullptr, pb[i]};
+          std::vector<float> ms;
+          for (int r = 0; r < reps + 2 && result == BREV_OK; ++r) {
+            cudaMemsetAsync(fl, r & 0xFF, flush_bytes, st);
+            cudaEventRecord(e0, st);
+            result = launch_choice(c, a, a, k, E, st);
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+              result = cuda_error(cudaGetLastError(), "autotune timing");
+              break;
+            }
+            float m = 0;
+            cudaEventElapsedTime(&m, e0, e1);
+            if (r >= 2) ms.push_back(m);
+          }
+          if (result != BREV_OK) break;
+          std::sort(ms.begin(), ms.end());
+          const double med = ms[ms.size() / 2];
+          if (med < best) {
+            best = med;
+            bbx = bbz = pb[i];
+            bord = 2;
+          }
+        }
+        if (result != BREV_OK) break;
         // keep the built-in shape unless another one is clearly faster:
         // small arrays are launch-latency bound and their timings differ
         // by noise only

@@ -842,6 +842,58 @@ brev_status batched_launch_forced(const BatchItem* items, int count, int b,
   return s;
 }
 
+// ---------------------------------------- single arrays on the pipeline --
+// In-place bit reversal of one array as a one-descriptor launch of the
+// batched kernel (descriptor passed by value): the tuner's "TMA pipeline"
+// candidate (launch order 2) beside the LSU tile kernels.
+bool pipeline_shape_ok(int k, int E, int b) { return b > 0 && batched_b_valid(k, E, b); }
+
+int pipeline_shapes(int E, int* out) {
+  int n = 0;
+  for (int b = 1; b <= 6; ++b)
+    if ((E == 4 || E == 8 || E == 16) && batched_shape_ok(E, b)) out[n++] = b;
+  return n;
+}
+
+brev_status bitrev_inplace_pipelined(void* data, int k, int E, int b, cudaStream_t stream) {
+  if (!pipeline_shape_ok(k, E, b) || ((uintptr_t)data % 16) != 0)
+    return set_error(BREV_ERR_UNSUPPORTED, "TMA pipeline: k=%d E=%d b=%d", k, E, b);
+  BatchDesc d{};
+  d.ptr = (char*)data;
+  d.k = k;
+  d.E = E;
+  d.b = b;
+  d.mode = BATCH_BITREV;
+  const int w = k - 2 * b;
+  const unsigned long long units = (unsigned long long)count_lt(w) + count_self(w);
+  if (units > 0xFFFFFFFFull) return set_error(BREV_ERR_UNSUPPORTED, "too many tile units");
+  d.units = (unsigned)units;
+  // about 8 tickets per resident CTA (the tail of the last wave stays short)
+  const unsigned stage = stage_unit_bytes(k, E, b);
+  const unsigned long long ctas = (unsigned long long)batched_grid(BATCH_STAGES * stage);
+  const unsigned long long unit_bytes = 2ull * ((unsigned long long)E << (2 * b));
+  d.grain = (unsigned)std::min<unsigned long long>(
+      std::max<unsigned long long>(1, units / (8 * ctas)),
+      std::max<unsigned long long>(1, BATCH_TICKET_BYTES / unit_bytes));
+  d.first_ticket = 0;
+  const unsigned long long tickets = (units + d.grain - 1) / d.grain;
+  void* ws = nullptr;
+  cudaError_t e = cudaMallocAsync(&ws, 16, stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(BREV_ERR_OOM, "pipeline workspace: %s", cudaGetErrorString(e));
+  }
+  auto* d_ticket = reinterpret_cast<unsigned long long*>(ws);
+  e = cudaMemsetAsync(d_ticket, 0, sizeof(unsigned long long), stream);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(ws, stream);
+    return cuda_error(e, "ticket reset");
+  }
+  brev_status st = launch_batched_kernel(nullptr, 0, tickets, d_ticket, stage, stream, &d);
+  cudaFreeAsync(ws, stream);
+  return st;
+}
+
 size_t batched_ws_bytes(int count) {
   return ((size_t)std::max(count, 0) * sizeof(BatchDesc) + 15) / 16 * 16 + 64;
 }

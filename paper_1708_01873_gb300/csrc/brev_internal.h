@@ -124,6 +124,11 @@ brev_status resident_launch(ResidentState* st, cudaStream_t stream, unsigned lon
 // Units, grain and tile exponent of a request in the resident kernel;
 // false if it cannot run there (elem sizes 1, 2; k <= 1).
 bool resident_shape(int k, int E, int ctas, int* b, unsigned* units, unsigned* grain);
+// Single arrays on the pipeline (launch order 2): valid tile exponents,
+// the list of them for E, and the launch.
+bool pipeline_shape_ok(int k, int E, int b);
+int pipeline_shapes(int E, int* out);
+brev_status bitrev_inplace_pipelined(void* data, int k, int E, int b, cudaStream_t stream);
 // Tuned batched tile exponent for (k, E), or -1 (brev_api.cu).
 int tuned_batched_b(int k, int E);
 // Argument checks of a batch (sizes, alignment, device ranges, no overlap).

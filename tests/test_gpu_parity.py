@@ -204,7 +204,10 @@ def test_error_statuses_launch_nothing(brev_lib, cuda_device):
     assert L.brev_permute_to(cpu.data_ptr(), cpu.data_ptr(), 10, 8, None) == 1  # host ptr
     assert L.brev_permute_shape(p, p, 10, 8, 4, 5, 0, None) == 1  # in-place needs square
     assert L.brev_permute_shape(p, p, 10, 8, 9, 9, 0, None) == 1  # tile larger than array
-    assert L.brev_permute_shape(p, p, 10, 8, 5, 5, 2, None) == 1  # no such order
+    assert L.brev_permute_shape(p, p, 10, 8, 5, 5, 3, None) == 1  # no such order
+    q = device_array(4, 10, 8)
+    assert L.brev_permute_shape(q.data_ptr(), p, 10, 8, 5, 5, 2, None) == 6  # pipeline: in place only
+    assert L.brev_permute_shape(p, p, 10, 8, 3, 3, 2, None) == 6  # b the pipeline does not stage
     assert brev_lib.brev_launch_count() == c0
     with pytest.raises(brev_lib.BrevError) as ei:
         brev_lib.brev_permute_shape(t, t, 3, 3)                # 64 B rows: not compiled
