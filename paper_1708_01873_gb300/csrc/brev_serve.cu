@@ -104,6 +104,7 @@ constexpr unsigned kResidentRing = 4096;
 constexpr unsigned kResidentTickets = 1u << 22;
 constexpr unsigned long long kResidentIdleNs = 2000000000ull;
 constexpr double kResidentStopIdle = 0.5;  // seconds
+constexpr double kLivenessCheck = 0.05;    // seconds without progress before asking the stream
 
 struct Inflight {
   cudaEvent_t ev;
@@ -222,7 +223,7 @@ brev_status run_resident(brev_server* srv, std::vector<Req>& reqs, int hold_resu
   // only fires if this thread stalls); the next request launches it again,
   // with sequence numbers and tickets counted from 0.
   bool running = false;
-  double last_busy = 0;
+  double last_busy = 0, last_progress = 0;
   const double idle_stop =
       srv->cfg.idle_stop_ms > 0 ? srv->cfg.idle_stop_ms * 1e-3 : kResidentStopIdle;
   auto stop_kernel = [&]() -> cudaError_t {
@@ -245,6 +246,7 @@ brev_status run_resident(brev_server* srv, std::vector<Req>& reqs, int hold_resu
       }
       Req& r = reqs[live[i].req];
       r.done = r.seen = now_s();
+      last_progress = r.done;
       lat_us.push_back((r.done - r.arrival) * 1e6);
       queue_us.push_back((r.launch - r.arrival) * 1e6);
       bytes_moved += 2 * ((uint64_t)r.E << r.k);
@@ -263,8 +265,12 @@ brev_status run_resident(brev_server* srv, std::vector<Req>& reqs, int hold_resu
         break;
       }
     }
-    // a kernel that ended with work outstanding gave up on a wait
-    if (!live.empty() && cudaStreamQuery(ks) != cudaErrorNotReady) {
+    // a kernel that ended with work outstanding gave up on a wait; asked
+    // only after kLivenessCheck s without progress, so that a healthy run
+    // makes no CUDA call between its launch and its stop (a CUDA call can
+    // block for tens of milliseconds when the driver is busy elsewhere)
+    if (!live.empty() && now - last_progress > kLivenessCheck &&
+        cudaStreamQuery(ks) != cudaErrorNotReady) {
       cudaGetLastError();
       result = set_error(BREV_ERR_CUDA,
                          "the resident serving kernel stopped with %zu requests in flight "
@@ -335,6 +341,7 @@ brev_status run_resident(brev_server* srv, std::vector<Req>& reqs, int hold_resu
     }
     if (result != BREV_OK) break;
     if (published) {
+      last_progress = now_s();
       __atomic_store_n(&R.h_ctl->requests, next_seq, __ATOMIC_RELEASE);
       ++publications;
       max_inflight = std::max(max_inflight, (int)live.size());
