@@ -370,7 +370,11 @@ class GpuBackend:
         return handle.query()
 
     def completion_time(self, handle) -> float:
-        return self.t_ref + self.ref.elapsed_time(handle) * 1e-3
+        # completion as the serving thread sees it (the clock its arrivals
+        # use), as the native loop reports; the device-clock time of the
+        # event would be read against a reference event that completed a
+        # few microseconds before t_ref, and so run late by that gap
+        return time.perf_counter()
 
     def release(self, handle) -> None:
         self._events.append(handle)
