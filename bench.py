@@ -337,29 +337,43 @@ def run_brev(args):
         if v["k"] >= 26:
             large[key] = round(v["bytes"] / (statistics.median(v["ms"]) * 1e-3) / 1e9, 1)
 
+    # The sections after the sweep report an error in their place rather
+    # than ending the run: the sweep's line is printed whatever they do.
+    def section(name, fn):
+        try:
+            return fn()
+        except Exception as exc:  # noqa: BLE001 -- reported in the JSON line
+            import traceback
+            traceback.print_exc()
+            return {"error": f"{name}: {type(exc).__name__}: {exc}"}
+
     # ---------------------------------------------------- batched (cfg 4)
     batched = None
     if not args.no_batched:
-        batched = bench_batched(torch, brev, inputs, device, stream, sampler, reduce_max,
-                                barrier, count=args.batch_count, kmax=args.batch_kmax)
+        batched = section("batched", lambda: bench_batched(
+            torch, brev, inputs, device, stream, sampler, reduce_max, barrier,
+            count=args.batch_count, kmax=args.batch_kmax))
 
     # ------------------------------------- large single arrays (cfg 3)
     large_cfg = None
     if not args.no_large:
-        large_cfg = bench_large(torch, brev, inputs, device, stream, sampler, reduce_max,
-                                barrier, peak, info["nominal_gbs"])
+        large_cfg = section("large", lambda: bench_large(
+            torch, brev, inputs, device, stream, sampler, reduce_max, barrier, peak,
+            info["nominal_gbs"]))
 
     # -------------------------------------------- widened rows (NEXT)
     next_rows = None
     if not args.no_next:
-        next_rows = bench_next(torch, brev, inputs, device, stream, sampler, reduce_max,
-                               barrier, peak, k=args.next_k)
+        next_rows = section("next", lambda: bench_next(
+            torch, brev, inputs, device, stream, sampler, reduce_max, barrier, peak,
+            k=args.next_k))
 
     # ------------------------------------------------------------ e2e
     e2e = None
     if not args.no_e2e:
-        e2e = bench_e2e(torch, brev, inputs, pts, seq, args.e2e_steps, stream, sampler,
-                        reduce_max, barrier, ws)
+        e2e = section("e2e", lambda: bench_e2e(
+            torch, brev, inputs, pts, seq, args.e2e_steps, stream, sampler, reduce_max,
+            barrier, ws))
     # ---------------------------------------------------- serving (cfg 5)
     serving = None
     if not args.no_serve:
@@ -369,14 +383,15 @@ def run_brev(args):
         torch.cuda.empty_cache()
         sampler.pause()
         arena = torch.empty(16 << 30, dtype=torch.uint8, device=device)
-        native, _ = brev.brev_server_run_poisson(arena, seed=5, rate_per_s=20000.0,
-                                                 seconds=args.serve_seconds)
-        resident, _ = brev.brev_server_run_poisson(arena, seed=5, rate_per_s=20000.0,
-                                                   seconds=args.serve_seconds, resident=True)
+        native = section("serving", lambda: brev.brev_server_run_poisson(
+            arena, seed=5, rate_per_s=20000.0, seconds=args.serve_seconds)[0])
+        resident = section("resident serving", lambda: brev.brev_server_run_poisson(
+            arena, seed=5, rate_per_s=20000.0, seconds=args.serve_seconds, resident=True)[0])
         del arena
         torch.cuda.empty_cache()
-        py = serve_poisson(seconds=min(args.serve_seconds, 5.0), rate=20000.0, seed=5,
-                           pool_bytes=16 << 30, device=local)
+        py = section("python serving", lambda: serve_poisson(
+            seconds=min(args.serve_seconds, 5.0), rate=20000.0, seed=5, pool_bytes=16 << 30,
+            device=local))
         sampler.resume()
         serving = {k: (round(v, 1) if isinstance(v, float) else v) for k, v in native.items()}
         serving["loop"] = "native C++ (brev_server_run_poisson)"
@@ -391,15 +406,15 @@ def run_brev(args):
                     "per request)",
             **{k: (round(v, 1) if isinstance(v, float) else v) for k, v in resident.items()
                if k in ("completed", "p50_us", "p99_us", "max_us", "mean_us", "queue_p99_us",
-                        "gbs", "launches", "max_inflight", "peak_pool_bytes")}}
+                        "gbs", "launches", "max_inflight", "peak_pool_bytes", "error")}}
         serving["python_loop"] = {k: py[k] for k in ("completed", "p50_us", "p99_us", "gbs",
-                                                     "mean_batch")}
+                                                     "mean_batch", "error") if k in py}
     sampler.stop()
     clocks = sampler.summary()
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        cpu = cpu_baseline(args.cpu_seconds)
+        cpu = section("cpu baseline", lambda: cpu_baseline(args.cpu_seconds))
 
     for p in pts:
         p["src"] = p["dst"] = None
