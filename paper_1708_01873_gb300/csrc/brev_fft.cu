@@ -197,11 +197,20 @@ __device__ __forceinline__ void dit_stages(uint4* sm, int nt, int S, int inverse
   }
 }
 
+#ifndef BREV_FFT_OOP_THREADS_MULT
+#define BREV_FFT_OOP_THREADS_MULT 1
+#endif
 template <int E, int B>
-__global__ void __launch_bounds__(Geom<E, 16, B, B>::THREADS, BREV_FFT_MIN_CTAS)
+__host__ __device__ constexpr int fft_oop_threads() {
+  return Geom<E, 16, B, B>::THREADS * BREV_FFT_OOP_THREADS_MULT;
+}
+
+template <int E, int B>
+__global__ void __launch_bounds__(fft_oop_threads<E, B>(), BREV_FFT_MIN_CTAS)
     k_fft_oop(char* __restrict__ dst, const char* __restrict__ src, int k, int S,
               int inverse) {
   using G = Geom<E, 16, B, B>;
+  constexpr int NTHR = fft_oop_threads<E, B>();
   using T = typename Cplx<E>::T;
   extern __shared__ uint4 smem_u4[];
   T* tw = reinterpret_cast<T*>(smem_u4 + G::CHUNKS);
@@ -212,10 +221,10 @@ __global__ void __launch_bounds__(Geom<E, 16, B, B>::THREADS, BREV_FFT_MIN_CTAS)
   const uint32_t y = blockIdx.x;
   const uint32_t ry = rev_bits(y, wy);
   const uint64_t stride = (uint64_t)E << (k - B);
-  load_tiles<G, true, G::THREADS, 1>(smem_u4, src + ((uint64_t)y << B) * E, nullptr, stride, 1);
+  load_tiles<G, true, NTHR, 1>(smem_u4, src + ((uint64_t)y << B) * E, nullptr, stride, 1);
   __syncthreads();
-  dit_stages<G, G::THREADS>(smem_u4, 1, S, inverse, tw);
-  store_tile<G, G::THREADS>(smem_u4, dst + ((uint64_t)ry << B) * E, stride);
+  dit_stages<G, NTHR>(smem_u4, 1, S, inverse, tw);
+  store_tile<G, NTHR>(smem_u4, dst + ((uint64_t)ry << B) * E, stride);
 }
 
 // In place: NTHR threads; each FFT pass takes the groups of both staged
@@ -321,8 +330,8 @@ struct FftKernel {
 template <int E, int B>
 static FftKernel fft_k() {
   using G = Geom<E, 16, B, B>;
-  return {(const void*)&k_fft_oop<E, B>, (const void*)&k_fft_inplace<E, B>, B, G::THREADS,
-          fft_ip_threads<E, B>(), G::TILE_BYTES};
+  return {(const void*)&k_fft_oop<E, B>, (const void*)&k_fft_inplace<E, B>, B,
+          fft_oop_threads<E, B>(), fft_ip_threads<E, B>(), G::TILE_BYTES};
 }
 
 static bool fft_lookup(int E, int B, FftKernel* out) {
