@@ -88,7 +88,10 @@ BREV_API brev_status brev_permute(void *data, int log2n, int elem_bytes, int in_
  * whose methods handle one array).  ptr_array[i] is a device pointer to
  * 2^log2n_array[i] elements of elem_bytes bytes.  ptr_array and
  * log2n_array are HOST arrays, read before the call returns.  Arrays must
- * not overlap one another.  count == 0 is a no-op. */
+ * not overlap one another.  count == 0 is a no-op.  The call uploads the
+ * batch's descriptors from pageable host memory into stream-ordered
+ * workspace, so it cannot be captured into a CUDA graph: capture a plan
+ * (brev_plan_create) instead. */
 BREV_API brev_status brev_permute_batched(void *const *ptr_array, const int *log2n_array,
                                  int count, int elem_bytes, void *stream);
 
