@@ -171,6 +171,13 @@ def test_resident_server_production_rate(brev_lib, cuda_device):
     assert stats["device_p50_us"] == stats["p50_us"]
     assert stats["launches"] == 1
     assert brev_lib.brev_wait_timeouts() == t0
+    with pytest.raises(brev_lib.BrevError):   # held results that cannot fit: refused, no hang
+        brev_lib.brev_server_run_poisson(arena[: 64 << 20], seed=1, rate_per_s=20000.0,
+                                         seconds=0.2, k_range=(20, 22), hold_results=True,
+                                         resident=True)
+    x = torch.empty(1 << 20, dtype=torch.complex64, device="cuda")   # the device still works
+    brev_lib.brev_permute(x, in_place=True)
+    torch.cuda.synchronize()
     with pytest.raises(brev_lib.BrevError):   # more slots than the request ring
         brev_lib.brev_server_run_poisson(arena[: 64 << 20], seed=1, rate_per_s=1000.0,
                                          seconds=0.01, max_slots=5000, resident=True)
