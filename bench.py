@@ -746,16 +746,39 @@ def largest_k_within(budget_s):
     return last_k, pts_all
 
 
+def time_oracle_mt(points, threads):
+    """The oracle's threaded out-of-place copy (index range split over
+    ``threads`` host threads) on every point; returns (algorithmic bytes,
+    seconds, threads actually used)."""
+    import oracle
+    nbytes, secs, used = 0, 0.0, 1
+    for kind, E, k, src in points:
+        t0 = time.perf_counter()
+        _, u = oracle.brev_oop_mt(src, k, E, threads)
+        secs += time.perf_counter() - t0
+        used = max(used, u)
+        nbytes += 2 * (1 << k) * E
+    return nbytes, secs, used
+
+
 def cpu_baseline(budget_s):
     """The plain single-thread oracle timed on the host cores over the sweep
-    truncated at the largest k that fits about ``budget_s`` seconds."""
+    truncated at the largest k that fits about ``budget_s`` seconds; beside
+    it, the oracle's threaded out-of-place copy on the same points with every
+    host thread."""
     kmax, pts = largest_k_within(budget_s / 2)
     nbytes, secs = time_oracle(pts)
+    threads = os.cpu_count() or 1
+    mt_bytes, mt_secs, used = time_oracle_mt(pts, threads)
     return {"value": round(nbytes / secs / 1e9, 3), "unit": "GB/s", "cores": 1,
             "kind": "oracle",
             "sample": f"sweep k=10..{kmax} x {{u32,f32,c64,c128}} x {{oop,in-place}}, "
                       f"plain single-thread C oracle, {secs:.1f} s timed",
-            "seconds": round(secs, 2)}
+            "seconds": round(secs, 2),
+            "threaded": {"value": round(mt_bytes / mt_secs / 1e9, 3), "unit": "GB/s",
+                         "cores": used, "host_threads": threads,
+                         "sample": f"the same points, out of place only, index range split "
+                                   f"over {used} threads, {mt_secs:.2f} s timed"}}
 
 
 def run_reference(args):
