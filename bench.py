@@ -35,6 +35,10 @@ sys.path.insert(0, ROOT)
 SWEEP_KS = list(range(10, 29))
 SWEEP_KINDS = [("u32", 4), ("f32", 4), ("c64", 8), ("c128", 16)]
 FALLBACK_PEAK_GBS = 6800.0
+# FP64 FMA thread-instructions per SM per cycle on GB300 (ncu's issue peak,
+# sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained = 304 over
+# 152 SMs)
+FP64_FMA_PER_SM_CLK = 2
 
 
 # ------------------------------------------------------------- helpers --
@@ -563,7 +567,13 @@ def bench_next(torch, brev, inputs, device, stream, sampler, reduce_max, barrier
         "ratio": round(rec / one, 3),
         "one_pass_gbs": round(nbytes / (one * 1e-3) / 1e9, 1),
         "recursive_hbm_passes": 3}
-    # bit reversal fused with the first DIT FFT stages vs the plain permutation
+    # bit reversal fused with the first DIT FFT stages vs the plain permutation.
+    # complex<double> stages are bound by the FP64 pipe: its peak is the SM
+    # count x 2 FP64 FMA per SM per cycle (the issue peak ncu reports for
+    # GB300) x 2 flops x the maximum SM clock nvidia-smi reports.
+    sm_count = torch.cuda.get_device_properties(device).multi_processor_count
+    max_mhz = max((smp[2] for smp in sampler.samples), default=None)
+    fp64_peak = sm_count * FP64_FMA_PER_SM_CLK * 2 * max_mhz * 1e6 / 1e12 if max_mhz else None
     for kind, E, S in (("c64", 8, 6), ("c128", 16, 5)):
         k2 = k
         x = torch.empty((1 << k2) * E, dtype=torch.uint8, device=device)
@@ -581,6 +591,14 @@ def bench_next(torch, brev, inputs, device, stream, sampler, reduce_max, barrier
             "fused_frac": round(nb / (fused * 1e-3) / 1e9 / peak, 4),
             "fused_gflops": round(flops / (fused * 1e-3) / 1e9, 1),
             "stages_cost_vs_permute": round(fused / plain, 3)}
+        if E == 16 and fp64_peak:
+            ach = flops / (fused * 1e-3) / 1e12
+            out[f"fft_stages_{kind}_k{k2}_S{S}"]["roofline"] = {
+                "bound": "alu", "unit": "TFLOP/s", "achieved": round(ach, 3),
+                "peak": round(fp64_peak, 3), "frac": round(ach / fp64_peak, 4),
+                "counted": "5 n flops per radix-2 stage",
+                "peak_source": f"{sm_count} SMs x {FP64_FMA_PER_SM_CLK} FP64 FMA/SM/cycle x 2 flops "
+                               f"x {max_mhz:.0f} MHz (derived)"}
         del x, y
     del src, dst
     return out

@@ -51,48 +51,92 @@ __device__ __forceinline__ void fill_twiddles(typename Cplx<E>::T* tw) {
   }
 }
 
-template <class T>
-__device__ __forceinline__ void butterfly(T& a, T& b, T w) {
-  T t;
-  t.x = b.x * w.x - b.y * w.y;
-  t.y = b.x * w.y + b.y * w.x;
-  b.x = a.x - t.x;
-  b.y = a.y - t.y;
-  a.x = a.x + t.x;
-  a.y = a.y + t.y;
+__device__ __forceinline__ float fmad(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmad(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// x with its sign bit XORed with bit 31 of m (m = 0 or 0x80000000): an
+// integer operation, so that conjugating costs no floating-point issue slot.
+__device__ __forceinline__ float flip_sign(float x, uint32_t m) {
+  return __uint_as_float(__float_as_uint(x) ^ m);
+}
+__device__ __forceinline__ double flip_sign(double x, uint32_t m) {
+  return __hiloint2double(__double2hiint(x) ^ (int)m, __double2loint(x));
 }
 
-// a * w for w = exp(-+2 pi i jj / 2^s) when jj is known at compile time:
-// w = 1 and w = -i (+i inverse) need no multiplication.
-template <class T, int S, int JJ>
-__device__ __forceinline__ T twiddle_const(T b, int inverse, const T* tw, int shift) {
-  if constexpr (JJ == 0) {
-    return b;
-  } else if constexpr (2 * JJ == (1 << (S - 1))) {  // a quarter turn
-    T t;
-    if (inverse) {  // +i b
-      t.x = -b.y;
-      t.y = b.x;
-    } else {  // -i b
-      t.x = b.y;
-      t.y = -b.x;
-    }
-    return t;
+// a' = a + w b, b' = a - w b.  In double precision a' takes two fused
+// multiply-adds per component (a.x - b.y w.y + b.x w.x, a.y + b.y w.x +
+// b.x w.y) and b' one more, as 2a - a': six operations, against eight for
+// the complex product followed by a sum and a difference.  This is the
+// standard rewrite of the radix-2 butterfly for multiply-add units.  The FP64
+// issue rate bounds the complex<double> stages, so the operation count is
+// the time.  Each component of a' is rounded twice (at most about 1 ulp of
+// |a| + |b|) and b' once more, so the per-stage error stays within that of
+// the plain form.  complex<float> keeps the plain form: its stages are
+// latency-bound, not FP32-bound, and the plain form holds the 5-CTA
+// register budget without spilling.
+template <class T>
+__device__ __forceinline__ void butterfly(T& a, T& b, T w) {
+  using R = decltype(a.x);
+  if constexpr (sizeof(R) == 8) {
+    const R px = fmad(b.x, w.x, fmad(-b.y, w.y, a.x));
+    const R py = fmad(b.x, w.y, fmad(b.y, w.x, a.y));
+    b.x = fmad(R(2), a.x, -px);
+    b.y = fmad(R(2), a.y, -py);
+    a.x = px;
+    a.y = py;
   } else {
-    T w = tw[JJ << shift];
-    if (inverse) w.y = -w.y;
     T t;
     t.x = b.x * w.x - b.y * w.y;
     t.y = b.x * w.y + b.y * w.x;
-    return t;
+    b.x = a.x - t.x;
+    b.y = a.y - t.y;
+    a.x = a.x + t.x;
+    a.y = a.y + t.y;
+  }
+}
+
+// The forward butterfly of stage S with twiddle w = exp(-2 pi i JJ / 2^S)
+// known at compile time (S <= 3): w = 1 and the quarter turn w = -i need
+// only a sum and a difference; the eighth turns of stage 3 (JJ = 1, 3) are
+// (+-1 - i)/sqrt 2, i.e. w b = sqrt(1/2) (s, d) or sqrt(1/2) (d, -s) with
+// s = b.x + b.y, d = b.y - b.x, which two additions and the multiply-add
+// form above finish.
+template <class T, int S, int JJ>
+__device__ __forceinline__ void butterfly_const(T& a, T& b) {
+  using R = decltype(a.x);
+  static_assert(S >= 1 && S <= 3 && JJ >= 0 && 2 * JJ < (1 << S), "first-pass twiddle");
+  if constexpr (JJ == 0) {
+    const T t = b;
+    b.x = a.x - t.x;
+    b.y = a.y - t.y;
+    a.x = a.x + t.x;
+    a.y = a.y + t.y;
+  } else if constexpr (2 * JJ == (1 << (S - 1))) {  // a quarter turn: -i b = (b.y, -b.x)
+    const T t = b;
+    b.x = a.x - t.y;
+    b.y = a.y + t.x;
+    a.x = a.x + t.y;
+    a.y = a.y - t.x;
+  } else {  // an eighth turn (S == 3, JJ odd)
+    const R c = R(0.70710678118654752440);  // sqrt(1/2)
+    const R s = b.x + b.y, d = b.y - b.x;
+    const R re = JJ == 1 ? s : d, im = JJ == 1 ? d : -s;  // (w b) / sqrt(1/2)
+    const R px = fmad(c, re, a.x);
+    const R py = fmad(c, im, a.y);
+    b.x = fmad(R(2), a.x, -px);
+    b.y = fmad(R(2), a.y, -py);
+    a.x = px;
+    a.y = py;
   }
 }
 
 // Stages 1..R (R <= 3) of every output row, in registers, with the
 // twiddles resolved at compile time (groups are 2^R consecutive elements).
+// Imaginary parts have their sign flipped by conj_in on loading and by
+// conj_out on storing.
 template <class G, int NTHR, int R>
-__device__ __forceinline__ void dit_first_pass(uint4* sm0, int nt, int inverse,
-                                               const typename Cplx<G::E>::T* tw) {
+__device__ __forceinline__ void dit_first_pass(uint4* sm0, int nt, uint32_t conj_in,
+                                               uint32_t conj_out) {
   using T = typename Cplx<G::E>::T;
   constexpr int GN = 1 << R;
   constexpr int LOG_GROUPS = G::BX + G::BZ - R;  // groups per tile
@@ -103,36 +147,37 @@ __device__ __forceinline__ void dit_first_pass(uint4* sm0, int nt, int inverse,
     const int base = (g >> G::BZ) << R;
     T v[GN];
 #pragma unroll
-    for (int t = 0; t < GN; ++t) v[t] = *tile_elem<G>(sm, base + t, z);
+    for (int t = 0; t < GN; ++t) {
+      v[t] = *tile_elem<G>(sm, base + t, z);
+      v[t].y = flip_sign(v[t].y, conj_in);
+    }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
 #pragma unroll
       for (int t = 0; t < GN; ++t) {
         if (t & (1 << r)) continue;
-        T b = v[t + (1 << r)];
+        T& a = v[t];
+        T& b = v[t + (1 << r)];
         // stage s = r + 1: jj = t mod 2^r
-        T tb;
-        if (r == 0) tb = twiddle_const<T, 1, 0>(b, inverse, tw, G::BX - 1);
+        if (r == 0) butterfly_const<T, 1, 0>(a, b);
         else if (r == 1) {
-          if ((t & 1) == 0) tb = twiddle_const<T, 2, 0>(b, inverse, tw, G::BX - 2);
-          else tb = twiddle_const<T, 2, 1>(b, inverse, tw, G::BX - 2);
+          if ((t & 1) == 0) butterfly_const<T, 2, 0>(a, b);
+          else butterfly_const<T, 2, 1>(a, b);
         } else {
           switch (t & 3) {
-            case 0: tb = twiddle_const<T, 3, 0>(b, inverse, tw, G::BX - 3); break;
-            case 1: tb = twiddle_const<T, 3, 1>(b, inverse, tw, G::BX - 3); break;
-            case 2: tb = twiddle_const<T, 3, 2>(b, inverse, tw, G::BX - 3); break;
-            default: tb = twiddle_const<T, 3, 3>(b, inverse, tw, G::BX - 3); break;
+            case 0: butterfly_const<T, 3, 0>(a, b); break;
+            case 1: butterfly_const<T, 3, 1>(a, b); break;
+            case 2: butterfly_const<T, 3, 2>(a, b); break;
+            default: butterfly_const<T, 3, 3>(a, b); break;
           }
         }
-        T a = v[t];
-        v[t].x = a.x + tb.x;
-        v[t].y = a.y + tb.y;
-        v[t + (1 << r)].x = a.x - tb.x;
-        v[t + (1 << r)].y = a.y - tb.y;
       }
     }
 #pragma unroll
-    for (int t = 0; t < GN; ++t) *tile_elem<G>(sm, base + t, z) = v[t];
+    for (int t = 0; t < GN; ++t) {
+      v[t].y = flip_sign(v[t].y, conj_out);
+      *tile_elem<G>(sm, base + t, z) = v[t];
+    }
   }
 }
 
@@ -140,8 +185,10 @@ __device__ __forceinline__ void dit_first_pass(uint4* sm0, int nt, int inverse,
 // registers: each thread takes groups of 2^R elements of one shared-memory
 // column, X = base + j + t 2^s0 (t < 2^R), which those R stages combine only
 // among themselves (the radix-2^R view of R consecutive radix-2 stages).
+// Forward twiddles; imaginary parts have their sign flipped by conj_out on
+// storing.
 template <class G, int NTHR, int R>
-__device__ __forceinline__ void dit_pass(uint4* sm0, int nt, int s0, int inverse,
+__device__ __forceinline__ void dit_pass(uint4* sm0, int nt, int s0, uint32_t conj_out,
                                          const typename Cplx<G::E>::T* tw) {
   using T = typename Cplx<G::E>::T;
   constexpr int GN = 1 << R;
@@ -164,34 +211,42 @@ __device__ __forceinline__ void dit_pass(uint4* sm0, int nt, int s0, int inverse
       for (int t = 0; t < GN; ++t) {
         if (t & (1 << r)) continue;
         const int jj = (j + (t << s0)) & hmask;
-        T w = tw[jj << (G::BX - s)];
-        if (inverse) w.y = -w.y;
-        butterfly(v[t], v[t + (1 << r)], w);
+        butterfly(v[t], v[t + (1 << r)], tw[jj << (G::BX - s)]);
       }
     }
 #pragma unroll
-    for (int t = 0; t < GN; ++t) *tile_elem<G>(sm, base + j + (t << s0), z) = v[t];
+    for (int t = 0; t < GN; ++t) {
+      v[t].y = flip_sign(v[t].y, conj_out);
+      *tile_elem<G>(sm, base + j + (t << s0), z) = v[t];
+    }
   }
 }
 
 // Stages 1..S on every output row of a staged tile (columns of sm), three
 // at a time: the first pass with compile-time twiddles, later ones from the
-// table.
+// table.  The butterflies are always the forward ones.  The inverse stages
+// (conjugate twiddles) are conj(forward(conj(x))) exactly -- every operation
+// of the butterflies is odd in the imaginary parts and rounding to nearest
+// is symmetric -- so the first pass flips the sign of the imaginary parts it
+// loads and the last pass those it stores.
 template <class G, int NTHR>
 __device__ __forceinline__ void dit_stages(uint4* sm, int nt, int S, int inverse,
                                            const typename Cplx<G::E>::T* tw) {
   if (S <= 0) return;
+  const uint32_t conj = inverse ? 0x80000000u : 0u;
   const int R0 = S >= 3 ? 3 : S;
-  if (R0 == 3) dit_first_pass<G, NTHR, 3>(sm, nt, inverse, tw);
-  else if (R0 == 2) dit_first_pass<G, NTHR, 2>(sm, nt, inverse, tw);
-  else dit_first_pass<G, NTHR, 1>(sm, nt, inverse, tw);
+  const uint32_t conj_out0 = S == R0 ? conj : 0u;
+  if (R0 == 3) dit_first_pass<G, NTHR, 3>(sm, nt, conj, conj_out0);
+  else if (R0 == 2) dit_first_pass<G, NTHR, 2>(sm, nt, conj, conj_out0);
+  else dit_first_pass<G, NTHR, 1>(sm, nt, conj, conj_out0);
   __syncthreads();
   int s0 = R0;
   while (s0 < S) {
     const int R = S - s0 >= 3 ? 3 : S - s0;
-    if (R == 3) dit_pass<G, NTHR, 3>(sm, nt, s0, inverse, tw);
-    else if (R == 2) dit_pass<G, NTHR, 2>(sm, nt, s0, inverse, tw);
-    else dit_pass<G, NTHR, 1>(sm, nt, s0, inverse, tw);
+    const uint32_t conj_out = s0 + R == S ? conj : 0u;
+    if (R == 3) dit_pass<G, NTHR, 3>(sm, nt, s0, conj_out, tw);
+    else if (R == 2) dit_pass<G, NTHR, 2>(sm, nt, s0, conj_out, tw);
+    else dit_pass<G, NTHR, 1>(sm, nt, s0, conj_out, tw);
     s0 += R;
     __syncthreads();
   }

@@ -4,8 +4,9 @@ oracle (double precision).
 Tolerance (derived from the arithmetic): inputs lie in [-1, 1) per
 component.  After s stages every value is a sum of 2^s inputs times unit
 twiddles, so |value| <= 2^s * sqrt(2).  Each stage rounds a complex product
-(about 3 ulp) and a sum (1 ulp), so the error grows by at most
-4 eps * 2^s * sqrt(2) per stage, and after S stages the absolute error
+(about 3 ulp) and a sum (1 ulp) -- or, in the double-precision multiply-add
+form, two multiply-adds and 2a - a' (under 2 ulp) -- so the error grows by at
+most 4 eps * 2^s * sqrt(2) per stage, and after S stages the absolute error
 per component is below (S + 1) * 8 * eps * 2^S, with eps = 2^-24 for
 complex<float> (float arithmetic; the oracle is exact to 2^-53 by
 comparison) and 2^-53 for complex<double>.  Zero stages are the plain
@@ -44,7 +45,7 @@ def check(got_bytes, x, k, E, S, inverse, what):
 @pytest.mark.parametrize("E", (8, 16))
 def test_fused_stages_vs_oracle(brev_lib, oracle_lib, cuda_device, E):
     for k in list(range(0, 15)) + [17, 20]:
-        for S in sorted({0, 1, 3, min(k, 5), min(k, 6)}):
+        for S in sorted({0, 1, 2, 3, 4, min(k, 5), min(k, 6)}):  # every pass split
             if S > k:
                 continue
             for inplace in (False, True):
@@ -76,8 +77,10 @@ def test_full_fft_small_arrays(brev_lib, oracle_lib, cuda_device, E):
                            atol=tol(E, k) * 4)
 
 
-@pytest.mark.parametrize("k,E,S", [(26, 8, 6), (26, 16, 5), (27, 8, 5)])
-def test_fused_full_size_sampled_blocks(brev_lib, oracle_lib, cuda_device, k, E, S):
+@pytest.mark.parametrize("k,E,S,inverse", [(26, 8, 6, False), (26, 16, 5, False),
+                                           (27, 8, 5, False), (26, 16, 5, True),
+                                           (25, 8, 6, True)])
+def test_fused_full_size_sampled_blocks(brev_lib, oracle_lib, cuda_device, k, E, S, inverse):
     """After S stages, output block b (2^S elements) is the S-stage result of
     the inputs spaced n / 2^S apart starting at rev_{k-S}(b) (pinned on the
     oracle); sampled blocks are checked against the oracle on those inputs,
@@ -85,7 +88,7 @@ def test_fused_full_size_sampled_blocks(brev_lib, oracle_lib, cuda_device, k, E,
     seed = 7000 + k
     src = device_array(seed, k, E)
     out = torch.empty_like(src)
-    brev_lib.brev_fft_stages(out, src, S)
+    brev_lib.brev_fft_stages(out, src, S, inverse)
     torch.cuda.synchronize()
     n, m = 1 << k, 1 << S
     rng = np.random.default_rng(k)
@@ -95,7 +98,7 @@ def test_fused_full_size_sampled_blocks(brev_lib, oracle_lib, cuda_device, k, E,
         r = oracle_lib.rev_bits(b, k - S)
         idx = np.arange(r, n, n // m, dtype=np.uint64)
         sub = as_complex(inputs.elements_np(seed, idx, KIND[E]).reshape(-1), E)
-        exp = oracle_lib.fft_dit_stages(sub, S, S)
+        exp = oracle_lib.fft_dit_stages(sub, S, S, inverse)
         g = as_complex(got[b].cpu().numpy(), E)
         err = np.max(np.abs(g - exp))
         assert err <= tol(E, S), f"block {b}: {err:.3e}"

@@ -789,6 +789,89 @@ def test_fused_fft_register_passes():
             assert np.allclose(got, exp, atol=1e-12), (B, S)
 
 
+def _bfly_multiply_add(a, b, w):
+    """butterfly(): a' from two multiply-adds per component, b' = 2a - a'."""
+    px = b.real * w.real + (-b.imag * w.imag + a.real)
+    py = b.real * w.imag + (b.imag * w.real + a.imag)
+    return px + 1j * py, (2 * a.real - px) + 1j * (2 * a.imag - py)
+
+
+def _bfly_const(a, b, S, JJ):
+    """butterfly_const<S, JJ>(), forward: w = 1, the quarter turn -i, or an
+    eighth turn as sqrt(1/2) (re, im) from s = b.x + b.y, d = b.y - b.x."""
+    if JJ == 0 or 2 * JJ == 1 << (S - 1):
+        t = b if JJ == 0 else -1j * b
+        return a + t, a - t
+    assert S == 3 and JJ in (1, 3)
+    c = np.sqrt(0.5)
+    s, d = b.real + b.imag, b.imag - b.real
+    re, im = (s, d) if JJ == 1 else (d, -s)
+    px, py = c * re + a.real, c * im + a.imag
+    return px + 1j * py, (2 * a.real - px) + 1j * (2 * a.imag - py)
+
+
+def test_fused_fft_multiply_add_butterflies():
+    """The kernels' arithmetic forms -- forward butterflies only, with
+    compile-time twiddles in the first pass (w = 1, quarter and eighth turns)
+    and table twiddles with the double-precision multiply-add butterfly after
+    it (complex<float> keeps the textbook butterfly emulated above); the
+    inverse conjugates the imaginary parts on the first pass's loads and the
+    last pass's stores -- give the textbook DIT stages with
+    w = exp(-+2 pi i j / 2^s) for every B and S, both directions."""
+    rng = np.random.default_rng(7)
+    for B in (3, 4, 5, 6):
+        BZ = B
+        table = np.exp(-2j * np.pi * np.arange(1 << (B - 1)) / (1 << B))
+        for S in range(1, B + 1):
+            for inverse in (0, 1):
+                cols = rng.normal(size=(1 << BZ, 1 << B)) + 1j * rng.normal(size=(1 << BZ, 1 << B))
+                got = cols.copy()
+                conj = np.conj if inverse else (lambda x: x)
+                R0 = min(3, S)
+                last = conj if S == R0 else (lambda x: x)
+                for base in range(0, 1 << B, 1 << R0):  # dit_first_pass, all columns at once
+                    v = [conj(got[:, base + t]) for t in range(1 << R0)]
+                    for r in range(R0):
+                        for t in range(1 << R0):
+                            if t & (1 << r):
+                                continue
+                            v[t], v[t + (1 << r)] = _bfly_const(v[t], v[t + (1 << r)], r + 1,
+                                                                t & ((1 << r) - 1))
+                    for t in range(1 << R0):
+                        got[:, base + t] = last(v[t])
+                s0 = R0
+                while s0 < S:  # dit_pass
+                    R = min(3, S - s0)
+                    last = conj if s0 + R == S else (lambda x: x)
+                    for q in range(1 << (B - R)):
+                        j = q & ((1 << s0) - 1)
+                        base = (q >> s0) << (s0 + R)
+                        Xs = [base + j + (t << s0) for t in range(1 << R)]
+                        v = [got[:, X].copy() for X in Xs]
+                        for r in range(R):
+                            s = s0 + r + 1
+                            hmask = (1 << (s - 1)) - 1
+                            for t in range(1 << R):
+                                if t & (1 << r):
+                                    continue
+                                w = table[((j + (t << s0)) & hmask) << (B - s)]
+                                v[t], v[t + (1 << r)] = _bfly_multiply_add(v[t], v[t + (1 << r)],
+                                                                           w)
+                        for X, val in zip(Xs, v):
+                            got[:, X] = last(val)
+                    s0 += R
+                exp = cols.copy()
+                sign = 1 if inverse else -1
+                for s in range(1, S + 1):
+                    m, h = 1 << s, 1 << (s - 1)
+                    for base in range(0, 1 << B, m):
+                        for j in range(h):
+                            w = np.exp(sign * 2j * np.pi * j / m)
+                            a, b = exp[:, base + j].copy(), exp[:, base + j + h] * w
+                            exp[:, base + j], exp[:, base + j + h] = a + b, a - b
+                assert np.allclose(got, exp, atol=1e-12), (B, S, inverse)
+
+
 def test_fused_fft_pair_passes_cover_both_tiles():
     """In place, one pass loop runs the groups of both staged tiles of a
     pair: index gt -> tile gt >> LOG_GROUPS (at gt's tile offset), group
