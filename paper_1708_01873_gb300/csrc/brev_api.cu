@@ -59,6 +59,60 @@ static int e_index(int E) {
 static std::mutex g_mu;
 static std::set<std::pair<const void*, int>> g_smem_done;
 
+// Workspace pool.  Descriptor tables, ticket counters and staging buffers
+// are stream-ordered allocations from a pool the library owns (one per
+// device) that keeps up to BREV_WS_POOL_KEEP_BYTES reserved across
+// synchronisations.  The device's default pool returns its memory at every
+// synchronisation (release threshold 0), so the first stream-ordered
+// allocation after one maps memory again on the calling thread -- about
+// 0.1 ms on GB300, paid by every call made right after a synchronise while
+// the GPU waits.  Beyond the kept amount (the host path's staging buffer of
+// a large array) memory still goes back at synchronisation.  The caller's
+// default pool is left as it is.
+#ifndef BREV_WS_POOL_KEEP_BYTES
+#define BREV_WS_POOL_KEEP_BYTES (32ull << 20)
+#endif
+static std::vector<cudaMemPool_t> g_ws_pools;  // per device, created on first use
+
+static cudaError_t workspace_pool(cudaMemPool_t* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if ((int)g_ws_pools.size() <= dev) g_ws_pools.resize(dev + 1, nullptr);
+  if (!g_ws_pools[dev]) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    e = cudaMemPoolCreate(&pool, &props);
+    if (e != cudaSuccess) return e;
+    unsigned long long keep = BREV_WS_POOL_KEEP_BYTES;
+    e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) {
+      cudaMemPoolDestroy(pool);
+      return e;
+    }
+    g_ws_pools[dev] = pool;
+  }
+  *out = g_ws_pools[dev];
+  return cudaSuccess;
+}
+
+cudaError_t ws_alloc(void** p, size_t bytes, cudaStream_t stream) {
+  cudaMemPool_t pool = nullptr;
+  const cudaError_t e = workspace_pool(&pool);
+  if (e != cudaSuccess) return e;
+  return cudaMallocFromPoolAsync(p, bytes, pool, stream);
+}
+
+void ws_free(void* p, cudaStream_t stream) {
+  if (p) cudaFreeAsync(p, stream);
+}
+
 cudaError_t ensure_smem(const void* kernel, unsigned smem) {
   if (smem <= 48 * 1024) return cudaSuccess;
   int dev = 0;
@@ -511,7 +565,7 @@ brev_status brev_permute_host(void* dst_host, const void* src_host, int log2n, i
   }
   // Otherwise: copy in, permute in device memory, copy out.
   void* buf = nullptr;
-  cudaError_t e = cudaMallocAsync(&buf, bytes, st);
+  cudaError_t e = ws_alloc(&buf, bytes, st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return set_error(BREV_ERR_OOM, "device workspace of %llu bytes: %s",
@@ -524,7 +578,7 @@ brev_status brev_permute_host(void* dst_host, const void* src_host, int log2n, i
       e = cudaMemcpyAsync(dst_host, buf, bytes, cudaMemcpyDeviceToHost, st);
     }
   }
-  cudaFreeAsync(buf, st);
+  ws_free(buf, st);
   if (e != cudaSuccess) return cuda_error(e, "host-path copy");
   if (s != BREV_OK) return s;
   e = cudaStreamSynchronize(st);

@@ -824,7 +824,7 @@ brev_status batched_launch_forced(const BatchItem* items, int count, int b,
   // stream-ordered workspace: descriptors + ticket counter
   const size_t desc_bytes = p.desc.size() * sizeof(BatchDesc);
   void* ws = nullptr;
-  cudaError_t e = cudaMallocAsync(&ws, desc_bytes + 64, stream);
+  cudaError_t e = ws_alloc(&ws, desc_bytes + 64, stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return set_error(BREV_ERR_OOM, "batched workspace of %zu bytes: %s", desc_bytes + 64,
@@ -833,12 +833,12 @@ brev_status batched_launch_forced(const BatchItem* items, int count, int b,
   // pageable source: staged before the call returns
   e = cudaMemcpyAsync(ws, p.desc.data(), desc_bytes, cudaMemcpyHostToDevice, stream);
   if (e != cudaSuccess) {
-    cudaFreeAsync(ws, stream);
+    ws_free(ws, stream);
     return cuda_error(e, "descriptor upload");
   }
   auto* d_ticket = reinterpret_cast<unsigned long long*>((char*)ws + ((desc_bytes + 15) / 16) * 16);
   s = enqueue_batch(p, (const BatchDesc*)ws, d_ticket, stream);
-  cudaFreeAsync(ws, stream);
+  ws_free(ws, stream);
   return s;
 }
 
@@ -878,7 +878,7 @@ brev_status bitrev_inplace_pipelined(void* data, int k, int E, int b, cudaStream
   d.first_ticket = 0;
   const unsigned long long tickets = (units + d.grain - 1) / d.grain;
   void* ws = nullptr;
-  cudaError_t e = cudaMallocAsync(&ws, 16, stream);
+  cudaError_t e = ws_alloc(&ws, 16, stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return set_error(BREV_ERR_OOM, "pipeline workspace: %s", cudaGetErrorString(e));
@@ -886,11 +886,11 @@ brev_status bitrev_inplace_pipelined(void* data, int k, int E, int b, cudaStream
   auto* d_ticket = reinterpret_cast<unsigned long long*>(ws);
   e = cudaMemsetAsync(d_ticket, 0, sizeof(unsigned long long), stream);
   if (e != cudaSuccess) {
-    cudaFreeAsync(ws, stream);
+    ws_free(ws, stream);
     return cuda_error(e, "ticket reset");
   }
   brev_status st = launch_batched_kernel(nullptr, 0, tickets, d_ticket, stage, stream, &d);
-  cudaFreeAsync(ws, stream);
+  ws_free(ws, stream);
   return st;
 }
 
@@ -946,7 +946,7 @@ brev_status transpose_inplace_pipelined(void* data, int a, int E, cudaStream_t s
   // the descriptor travels by value; only the ticket counter needs
   // stream-ordered device memory (so the call can be captured in a graph)
   void* ws = nullptr;
-  cudaError_t e = cudaMallocAsync(&ws, 16, stream);
+  cudaError_t e = ws_alloc(&ws, 16, stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return set_error(BREV_ERR_OOM, "transposition workspace: %s", cudaGetErrorString(e));
@@ -954,12 +954,12 @@ brev_status transpose_inplace_pipelined(void* data, int a, int E, cudaStream_t s
   auto* d_ticket = reinterpret_cast<unsigned long long*>(ws);
   e = cudaMemsetAsync(d_ticket, 0, sizeof(unsigned long long), stream);
   if (e != cudaSuccess) {
-    cudaFreeAsync(ws, stream);
+    ws_free(ws, stream);
     return cuda_error(e, "ticket reset");
   }
   brev_status st = launch_batched_kernel(nullptr, 0, tickets, d_ticket,
                                          stage_unit_bytes(2 * b, E, b), stream, &d);
-  cudaFreeAsync(ws, stream);
+  ws_free(ws, stream);
   return st;
 }
 

@@ -55,6 +55,10 @@ cudaError_t ensure_smem(const void* kernel, unsigned smem);
 cudaError_t launch_pdl(const void* kern, unsigned grid, unsigned threads, void** args,
                        unsigned smem, cudaStream_t stream);
 int current_device_sm_count();
+// Stream-ordered workspace from the library's own memory pool on the current
+// device (brev_api.cu); released with ws_free on a stream.  Capturable.
+cudaError_t ws_alloc(void** p, size_t bytes, cudaStream_t stream);
+void ws_free(void* p, cudaStream_t stream);
 // Validate a device range (device or managed memory, inside one allocation).
 brev_status check_device_range(const void* p, uint64_t bytes, const char* what);
 

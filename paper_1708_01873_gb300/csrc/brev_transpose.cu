@@ -272,7 +272,7 @@ brev_status brev_permute_recursive(void* data, int log2n, int elem_bytes, void* 
   // each half takes the (k-1)-bit permutation (x y -> rev(y) rev(x))
   const uint64_t bytes = (uint64_t)E << k;
   void* ws = nullptr;
-  cudaError_t e = cudaMallocAsync(&ws, bytes, st);
+  cudaError_t e = ws_alloc(&ws, bytes, st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return set_error(BREV_ERR_OOM, "even-odd workspace: %s", cudaGetErrorString(e));
@@ -289,7 +289,7 @@ brev_status brev_permute_recursive(void* data, int log2n, int elem_bytes, void* 
     e = cudaMemcpyAsync(data, ws, bytes, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) s = cuda_error(e, "copy back");
   }
-  cudaFreeAsync(ws, st);
+  ws_free(ws, st);
   return s;
 }
 
