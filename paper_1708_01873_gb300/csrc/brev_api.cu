@@ -16,6 +16,7 @@
 
 #include "brev_device.cuh"
 #include "brev_internal.h"
+#include "brev_trace.h"
 
 namespace brev {
 
@@ -457,12 +458,14 @@ using namespace brev;
 extern "C" {
 
 brev_status brev_permute_to(void* dst, const void* src, int log2n, int elem_bytes, void* stream) {
+  BREV_TRACE("brev_permute_to");
   brev_status s = check_pair(dst, src, log2n, elem_bytes);
   if (s != BREV_OK) return s;
   return launch_single(dst, src, log2n, elem_bytes, (cudaStream_t)stream);
 }
 
 brev_status brev_permute(void* data, int log2n, int elem_bytes, int in_place, void* stream) {
+  BREV_TRACE("brev_permute");
   brev_status s = check_common(log2n, elem_bytes);
   if (s != BREV_OK) return s;
   if (!data) return set_error(BREV_ERR_INVALID_ARG, "NULL data pointer");
@@ -475,6 +478,7 @@ brev_status brev_permute(void* data, int log2n, int elem_bytes, int in_place, vo
 
 brev_status brev_permute_shape(void* dst, const void* src, int log2n, int elem_bytes, int bx,
                                int bz, int order, void* stream) {
+  BREV_TRACE("brev_permute_shape");
   brev_status s = check_pair(dst, src, log2n, elem_bytes);
   if (s != BREV_OK) return s;
   const bool inplace = dst == src;
@@ -511,6 +515,7 @@ brev_status brev_permute_shape(void* dst, const void* src, int log2n, int elem_b
 
 brev_status brev_permute_batched_mixed(void* const* ptr_array, const int* log2n_array,
                                        const int* elem_bytes_array, int count, void* stream) {
+  BREV_TRACE("brev_permute_batched_mixed");
   if (count < 0) return set_error(BREV_ERR_INVALID_ARG, "count=%d", count);
   if (count == 0) return BREV_OK;
   if (!ptr_array || !log2n_array || !elem_bytes_array)
@@ -525,6 +530,7 @@ brev_status brev_permute_batched_mixed(void* const* ptr_array, const int* log2n_
 
 brev_status brev_permute_batched(void* const* ptr_array, const int* log2n_array, int count,
                                  int elem_bytes, void* stream) {
+  BREV_TRACE("brev_permute_batched");
   if (count < 0) return set_error(BREV_ERR_INVALID_ARG, "count=%d", count);
   if (count == 0) return BREV_OK;
   std::vector<int> es(count, elem_bytes);
@@ -533,6 +539,7 @@ brev_status brev_permute_batched(void* const* ptr_array, const int* log2n_array,
 
 brev_status brev_permute_host(void* dst_host, const void* src_host, int log2n, int elem_bytes,
                               void* stream) {
+  BREV_TRACE("brev_permute_host");
   brev_status s = check_common(log2n, elem_bytes);
   if (s != BREV_OK) return s;
   if (!dst_host || !src_host) return set_error(BREV_ERR_INVALID_ARG, "NULL host pointer");
@@ -852,6 +859,7 @@ static brev_status autotune_batched(int k_min, int k_max, int E, cudaStream_t st
 }
 
 brev_status brev_autotune(int k_min, int k_max, int elem_bytes, const char* cache_path) {
+  BREV_TRACE("brev_autotune");
   if (!valid_E(elem_bytes)) return set_error(BREV_ERR_INVALID_ARG, "elem_bytes=%d", elem_bytes);
   if (k_min < 0 || k_max > BREV_MAX_LOG2N || k_min > k_max)
     return set_error(BREV_ERR_INVALID_ARG, "k range [%d, %d]", k_min, k_max);

@@ -20,6 +20,7 @@
 #include "brev_async.cuh"
 #include "brev_device.cuh"
 #include "brev_internal.h"
+#include "brev_trace.h"
 #include "brev_transpose_units.cuh"
 
 namespace brev {
@@ -1097,6 +1098,7 @@ using namespace brev;
 extern "C" brev_status brev_plan_create(void* const* ptr_array, const int* log2n_array,
                                         const int* elem_bytes_array, int elem_bytes, int count,
                                         brev_plan** out_plan) {
+  BREV_TRACE("brev_plan_create");
   if (!out_plan) return set_error(BREV_ERR_INVALID_ARG, "out_plan is NULL");
   *out_plan = nullptr;
   if (count < 0 || (count > 0 && (!ptr_array || !log2n_array)))
@@ -1192,6 +1194,7 @@ extern "C" brev_status brev_wait_timeouts(uint64_t* out) {
 }
 
 extern "C" brev_status brev_plan_launch(brev_plan* plan, void* stream) {
+  BREV_TRACE("brev_plan_launch");
   if (!plan || !plan->exec) return set_error(BREV_ERR_INVALID_ARG, "invalid plan");
   cudaError_t e = cudaGraphLaunch(plan->exec, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_error(e, "graph launch");
@@ -1267,6 +1270,7 @@ extern "C" brev_status brev_permute_batched_noalloc(void* const* ptr_array,
                                                     const int* log2n_array,
                                                     const int* elem_bytes_array, int count,
                                                     void* stream) {
+  BREV_TRACE("brev_permute_batched_noalloc");
   if (count < 0) return set_error(BREV_ERR_INVALID_ARG, "count=%d", count);
   if (count > NOALLOC_MAX_ARRAYS)
     return set_error(BREV_ERR_INVALID_ARG,

@@ -17,6 +17,7 @@
 
 #include "brev_device.cuh"
 #include "brev_internal.h"
+#include "brev_trace.h"
 
 namespace brev {
 
@@ -408,6 +409,7 @@ using namespace brev;
 
 extern "C" brev_status brev_fft_stages(void* dst, const void* src, int log2n, int elem_bytes,
                                        int stages, int inverse, void* stream) {
+  BREV_TRACE("brev_fft_stages");
   const int E = elem_bytes, k = log2n, S = stages;
   if (E != 8 && E != 16)
     return set_error(BREV_ERR_INVALID_ARG, "elem_bytes=%d (complex<float> 8 or complex<double> 16)",

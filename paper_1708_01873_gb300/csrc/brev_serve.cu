@@ -36,6 +36,7 @@
 #include <vector>
 
 #include "brev_internal.h"
+#include "brev_trace.h"
 
 namespace {
 
@@ -430,6 +431,7 @@ brev_status brev_server_run_poisson(brev_server* srv, uint64_t seed, double rate
                                     const int* elem_bytes, int n_elem_bytes, int hold_results,
                                     brev_server_request* trace, uint64_t trace_capacity,
                                     brev_server_stats* out) {
+  BREV_TRACE("brev_server_run_poisson");
   if (!srv || !out) return set_error(BREV_ERR_INVALID_ARG, "NULL server or stats");
   if (!(rate_per_s > 0) || !(seconds > 0) || k_min < 0 || k_max < k_min ||
       k_max > BREV_MAX_LOG2N || !elem_bytes || n_elem_bytes < 1)

@@ -15,6 +15,7 @@
 #include "brev_device.cuh"
 #include "brev_device_rt.cuh"
 #include "brev_internal.h"
+#include "brev_trace.h"
 #include "brev_transpose_units.cuh"
 
 namespace brev {
@@ -223,6 +224,7 @@ extern "C" {
 
 brev_status brev_transpose(void* dst, const void* src, int log2_rows, int log2_cols,
                            int elem_bytes, void* stream) {
+  BREV_TRACE("brev_transpose");
   if (log2_rows < 0 || log2_cols < 0)
     return set_error(BREV_ERR_INVALID_ARG, "log2_rows=%d log2_cols=%d", log2_rows, log2_cols);
   brev_status s = check_args(dst, src, log2_rows + log2_cols, elem_bytes);
@@ -234,18 +236,21 @@ brev_status brev_transpose(void* dst, const void* src, int log2_rows, int log2_c
 }
 
 brev_status brev_even_odd(void* dst, const void* src, int log2n, int elem_bytes, void* stream) {
+  BREV_TRACE("brev_even_odd");
   if (log2n < 1) return brev_transpose(dst, src, 0, 0, elem_bytes, stream);
   return brev_transpose(dst, src, log2n - 1, 1, elem_bytes, stream);
 }
 
 brev_status brev_perfect_shuffle(void* dst, const void* src, int log2n, int elem_bytes,
                                  void* stream) {
+  BREV_TRACE("brev_perfect_shuffle");
   if (log2n < 1) return brev_transpose(dst, src, 0, 0, elem_bytes, stream);
   return brev_transpose(dst, src, 1, log2n - 1, elem_bytes, stream);
 }
 
 brev_status brev_permute_segments(void* data, int log2_segments, int log2_seglen, int elem_bytes,
                                   void* stream) {
+  BREV_TRACE("brev_permute_segments");
   if (log2_segments < 0 || log2_seglen < 0)
     return set_error(BREV_ERR_INVALID_ARG, "log2_segments=%d log2_seglen=%d", log2_segments,
                      log2_seglen);
@@ -255,6 +260,7 @@ brev_status brev_permute_segments(void* data, int log2_segments, int log2_seglen
 }
 
 brev_status brev_permute_recursive(void* data, int log2n, int elem_bytes, void* stream) {
+  BREV_TRACE("brev_permute_recursive");
   brev_status s = check_args(data, data, log2n, elem_bytes);
   if (s != BREV_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
