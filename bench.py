@@ -3,8 +3,8 @@
 
 Default workload (one "step"): the single-array sweep
 k = 10..28 x {uint32, float32, complex<float>, complex<double>} x
-{out-of-place, in-place} -- 152 permutations of seeded synthetic arrays,
-34 GiB moved per step.  ``value`` is bit-reverse GB/s counting read + write
+{out-of-place, in-place} -- 152 permutations of seeded synthetic arrays
+held in 34 GiB, 64 GiB moved per step.  ``value`` is bit-reverse GB/s counting read + write
 (2 n E bytes per permutation) over the whole step.  The same JSON line also
 carries the batched workload (4096 arrays, k in [8, 20], mixed
 complex<float>/complex<double>: one captured-graph persistent launch vs a
@@ -204,6 +204,22 @@ def sweep_order(pts):
     return seq
 
 
+def sweep_config(kmax, kinds, ws, l2_mib):
+    """The sweep's `config`, shared by both arms: every kind's k = 10..kmax,
+    out of place then in place, 2 n E bytes per point."""
+    sel = [(kind, E) for kind, E in SWEEP_KINDS if kind in kinds.split(",")]
+    names = {"u32": "uint32", "f32": "float32", "c64": "complex<float>", "c128": "complex<double>"}
+    step_bytes = 2 * sum(2 * (1 << k) * E for _, E in sel for k in range(SWEEP_KS[0], kmax + 1))
+    return {"workload": "single-array sweep k=%d..%d x {%s} x {out-of-place, in-place}"
+                        % (SWEEP_KS[0], kmax, ", ".join(names[kd] for kd, _ in sel)),
+            "points_per_step": 2 * len(sel) * (kmax - SWEEP_KS[0] + 1),
+            "bytes_per_step": step_bytes,
+            "l2": "no flush: %.0f GiB moved per step, every buffer re-touched only after "
+                  ">= 1 GiB of other traffic (L2 = %s MiB)"
+                  % (step_bytes / 2 ** 30, l2_mib if l2_mib is not None else "?"),
+            "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"}
+
+
 def launch_point(brev, p, inplace, stream):
     if inplace:
         brev.lib().brev_permute_to(p["dst"].data_ptr(), p["dst"].data_ptr(), p["k"], p["E"],
@@ -243,6 +259,8 @@ def run_brev(args):
     pts = make_sweep(torch, inputs, args.kmax, device, args.kinds.split(","))
     seq = sweep_order(pts)
     step_bytes = sum(p["bytes"] for p, _ in seq)
+    if step_bytes != sweep_config(args.kmax, args.kinds, ws, None)["bytes_per_step"]:
+        raise RuntimeError("sweep bytes disagree with the reported config")
     names = [shape_name(brev, p["k"], p["E"], ip) for p, ip in seq]
     L = brev.lib()
     # Warm-up.  Its last steps bracket every launch with CUDA events: the
@@ -431,14 +449,7 @@ def run_brev(args):
             "dtype": "u8",
             "data": "synthetic (seeded SplitMix64: uint32, float32 U[-1,1), complex<float>, "
                     "complex<double>)",
-            "config": {"workload": "single-array sweep k=10..%d x {uint32, float32, "
-                                   "complex<float>, complex<double>} x {out-of-place, in-place}"
-                                   % args.kmax,
-                       "points_per_step": len(seq), "bytes_per_step": step_bytes,
-                       "l2": "no flush: 34 GiB moved per step, every buffer re-touched only "
-                             "after >= 1 GiB of other traffic (L2 = %d MiB)"
-                             % (info["l2_bytes"] >> 20),
-                       "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+            "config": sweep_config(args.kmax, args.kinds, ws, info["l2_bytes"] >> 20),
             "roofline": roofline,
             "frac_of_peak": round(value / ws / peak, 4),
             "frac_of_nominal": round(value / ws / info["nominal_gbs"], 4),
@@ -799,6 +810,18 @@ def cpu_baseline(budget_s):
                                    f"over {used} threads, {mt_secs:.2f} s timed"}}
 
 
+def reference_l2_mib():
+    """L2 size for the shared config line, if a GPU is visible (the oracle
+    itself needs none)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.get_device_properties(0).L2_cache_size >> 20
+    except Exception:  # noqa: BLE001 -- informational only
+        pass
+    return None
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -820,13 +843,12 @@ def run_reference(args):
             "ms_per_step": round(secs / args.steps * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8",
             "data": "synthetic (seeded SplitMix64)",
-            "config": {"workload": f"single-array sweep sample k=10..{kmax} x "
-                                   "{uint32, float32, complex<float>, complex<double>} x "
-                                   "{out-of-place, in-place} (bounded sample of the "
-                                   "k=10..28 sweep)"},
+            "config": sweep_config(args.kmax, args.kinds, ws, reference_l2_mib()),
             "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": 1,
                              "kind": "oracle",
-                             "sample": f"k=10..{kmax} per step, plain single-thread C oracle"},
+                             "sample": f"bounded sample of that sweep: each step the points "
+                                       f"k=10..{kmax} of every kind, out of place and in "
+                                       f"place, on the plain single-thread C oracle"},
             "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
