@@ -214,9 +214,12 @@ def sweep_config(kmax, kinds, ws, l2_mib):
                         % (SWEEP_KS[0], kmax, ", ".join(names[kd] for kd, _ in sel)),
             "points_per_step": 2 * len(sel) * (kmax - SWEEP_KS[0] + 1),
             "bytes_per_step": step_bytes,
-            "l2": "no flush: %.0f GiB moved per step, every buffer re-touched only after "
-                  ">= 1 GiB of other traffic (L2 = %s MiB)"
-                  % (step_bytes / 2 ** 30, l2_mib if l2_mib is not None else "?"),
+            "l2": ("no flush: %.0f GiB moved per step, every buffer re-touched only after "
+                   ">= 1 GiB of other traffic (L2 = %s MiB)"
+                   % (step_bytes / 2 ** 30, l2_mib if l2_mib is not None else "?"))
+                  if kmax >= 26 else
+                  "no flush: a reduced sweep of %.1f MiB per step, whose buffers can stay in L2"
+                  % (step_bytes / 2 ** 20),
             "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"}
 
 
