@@ -94,6 +94,18 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
+// Per-thread asynchronous 16-byte copy from global to shared memory,
+// cached in L2 only (both addresses 16-byte aligned); cp_async_wait_all
+// waits for all of this thread's copies, after which a barrier makes them
+// visible to the block.
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst_smem)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 // Ordered accesses for hand-offs between the host and a running kernel
 // (system scope: page-locked host memory) and between CTAs (GPU scope).
 __device__ __forceinline__ unsigned long long ld_acquire_sys(const unsigned long long* p) {
