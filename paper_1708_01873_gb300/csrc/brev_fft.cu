@@ -15,7 +15,6 @@
 // one pass for the permutation and another for the stages.
 #include <algorithm>
 
-#include "brev_async.cuh"
 #include "brev_device.cuh"
 #include "brev_internal.h"
 #include "brev_trace.h"
@@ -39,41 +38,6 @@ __device__ __forceinline__ typename Cplx<G::E>::T* tile_elem(uint4* sm, int X, i
   constexpr int LOG_V = ilog2c(G::V);
   const int chunk = X * G::CIN + ((z >> LOG_V) ^ ((X >> LOG_V) & G::SWZ));
   return reinterpret_cast<typename Cplx<G::E>::T*>(sm + chunk) + (z & (G::V - 1));
-}
-
-// Stage one or two tiles in the layout of the tile kernels' load_tiles --
-// source row x, 16-byte chunk c lands at shared row rev(x), swizzled chunk
-// c ^ ((rev(x) / V) & SWZ) -- with per-thread asynchronous copies.  No
-// registers hold data in flight, so every thread issues all its chunks of
-// the tile (or pair) at once: on GB300 this took the in-place complex<float>
-// kernel (6 stages, k = 28) from 0.85 to 0.66 ms and let the out-of-place
-// one run 6 CTAs per SM without spilling (0.70 to 0.65 ms), where the
-// register-staged loads kept at most 8 chunks per thread in flight.  The
-// caller's barrier follows.
-template <class G, int NTHR, int NT>
-__device__ __forceinline__ void load_tiles_async(uint4* sm, const char* src0, const char* src1,
-                                                 uint64_t row_stride, int nt_active) {
-  static_assert(G::W == 16, "16-byte chunks");
-  constexpr int PER = (G::CHUNKS + NTHR - 1) / NTHR;
-  const int tid = threadIdx.x;
-#pragma unroll
-  for (int t = 0; t < NT; ++t) {
-    if (t < nt_active) {
-      const char* base = t == 0 ? src0 : src1;
-#pragma unroll
-      for (int i = 0; i < PER; ++i) {
-        const int q = tid + i * NTHR;
-        if (G::CHUNKS % NTHR == 0 || q < G::CHUNKS) {
-          const int x = q >> G::LOG_CIN, c = q & (G::CIN - 1);
-          const int X = (int)rev_c<G::BX>((uint32_t)x);
-          const int pc = c ^ ((X / G::V) & G::SWZ);
-          cp_async16(sm + t * G::CHUNKS + X * G::CIN + pc,
-                     base + (uint64_t)x * row_stride + (unsigned)c * 16);
-        }
-      }
-    }
-  }
-  cp_async_wait_all();
 }
 
 // Twiddles w_{2^B}^i = exp(-2 pi i i / 2^B), i < 2^(B-1), into shared memory.
@@ -313,7 +277,7 @@ __global__ void __launch_bounds__(fft_oop_threads<E, B>(), BREV_FFT_MIN_CTAS)
   const uint32_t y = blockIdx.x;
   const uint32_t ry = rev_bits(y, wy);
   const uint64_t stride = (uint64_t)E << (k - B);
-  load_tiles_async<G, NTHR, 1>(smem_u4, src + ((uint64_t)y << B) * E, nullptr, stride, 1);
+  load_tiles<G, true, NTHR, 1>(smem_u4, src + ((uint64_t)y << B) * E, nullptr, stride, 1);
   __syncthreads();
   dit_stages<G, NTHR>(smem_u4, 1, S, inverse, tw);
   store_tile<G, NTHR>(smem_u4, dst + ((uint64_t)ry << B) * E, stride);
@@ -365,7 +329,7 @@ __global__ void __launch_bounds__(fft_ip_threads<E, B>(), fft_ip_min_ctas<E>())
   const uint64_t stride = (uint64_t)E << (k - B);
   char* const ty = data + ((uint64_t)y << B) * E;
   char* const tr = data + ((uint64_t)ry << B) * E;
-  load_tiles_async<G, NTHR, 2>(smem_u4, ty, tr, stride, nt);
+  load_tiles<G, false, NTHR, 2>(smem_u4, ty, tr, stride, nt);
   __syncthreads();
   dit_stages<G, NTHR>(smem_u4, nt, S, inverse, tw);  // both tiles in each pass
   store_tile<G, NTHR>(smem_u4, tr, stride);
