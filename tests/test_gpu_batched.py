@@ -205,6 +205,12 @@ def test_host_path(brev_lib, oracle_lib, cuda_device):
         brev_lib.brev_permute_host(p, p)
         assert_bytes_equal(p.view(torch.uint8).numpy(), oracle_lib.brev_oop(pb, k, E), E,
                            f"host path in place k={k} E={E}")
+        # in place on a page-locked buffer: the tile kernel reads and writes it directly
+        qb = host_array(90 + k, k, E)
+        q = torch.from_numpy(qb.copy()).view(DTYPE[E]).pin_memory()
+        brev_lib.brev_permute_host(q, q)
+        assert_bytes_equal(q.view(torch.uint8).numpy(), oracle_lib.brev_oop(qb, k, E), E,
+                           f"host path in place, page-locked, k={k} E={E}")
     L = brev_lib.lib()
     d = device_array(1, 10, 8)
     assert L.brev_permute_host(d.data_ptr(), d.data_ptr(), 10, 8, None) == 1  # device ptr
