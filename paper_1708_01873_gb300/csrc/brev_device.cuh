@@ -311,32 +311,32 @@ __device__ __forceinline__ void load_tiles(typename ChunkT<G::W>::type* sm,
       }
     }
     cp_async_wait_all();
-    return;
-  }
+  } else {
 #pragma unroll 1
-  for (int b0 = 0; b0 < TOTAL; b0 += BATCH) {
-    C r[BATCH];
+    for (int b0 = 0; b0 < TOTAL; b0 += BATCH) {
+      C r[BATCH];
 #pragma unroll
-    for (int j = 0; j < BATCH; ++j) {
-      const int f = b0 + j;
-      const int t = f / PER, i = f % PER;
-      const int q = tid + i * NTHR;
-      if (f < TOTAL && t < nt_active && (G::CHUNKS % NTHR == 0 || q < G::CHUNKS)) {
-        const int x = q >> G::LOG_CIN, c = q & (G::CIN - 1);
-        const char* base = (NT == 1 || t == 0) ? src0 : src1;
-        r[j] = gload<G::W, NC>(base + (uint64_t)x * row_stride + (unsigned)c * G::W);
+      for (int j = 0; j < BATCH; ++j) {
+        const int f = b0 + j;
+        const int t = f / PER, i = f % PER;
+        const int q = tid + i * NTHR;
+        if (f < TOTAL && t < nt_active && (G::CHUNKS % NTHR == 0 || q < G::CHUNKS)) {
+          const int x = q >> G::LOG_CIN, c = q & (G::CIN - 1);
+          const char* base = (NT == 1 || t == 0) ? src0 : src1;
+          r[j] = gload<G::W, NC>(base + (uint64_t)x * row_stride + (unsigned)c * G::W);
+        }
       }
-    }
 #pragma unroll
-    for (int j = 0; j < BATCH; ++j) {
-      const int f = b0 + j;
-      const int t = f / PER, i = f % PER;
-      const int q = tid + i * NTHR;
-      if (f < TOTAL && t < nt_active && (G::CHUNKS % NTHR == 0 || q < G::CHUNKS)) {
-        const int x = q >> G::LOG_CIN, c = q & (G::CIN - 1);
-        const int X = (int)rev_c<G::BX>((uint32_t)x);
-        const int pc = c ^ ((X / G::V) & G::SWZ);
-        sm[t * G::CHUNKS + X * G::CIN + pc] = r[j];
+      for (int j = 0; j < BATCH; ++j) {
+        const int f = b0 + j;
+        const int t = f / PER, i = f % PER;
+        const int q = tid + i * NTHR;
+        if (f < TOTAL && t < nt_active && (G::CHUNKS % NTHR == 0 || q < G::CHUNKS)) {
+          const int x = q >> G::LOG_CIN, c = q & (G::CIN - 1);
+          const int X = (int)rev_c<G::BX>((uint32_t)x);
+          const int pc = c ^ ((X / G::V) & G::SWZ);
+          sm[t * G::CHUNKS + X * G::CIN + pc] = r[j];
+        }
       }
     }
   }

@@ -37,30 +37,46 @@ __device__ __forceinline__ void load_tiles_g(typename ChunkT<W>::type* sm, const
   const int per = chunks >= NTHR ? chunks / NTHR : 1;
   const int total = per * nt;
   const int tid = threadIdx.x;
+  if constexpr (W == 16) {
 #pragma unroll 1
-  for (int b0 = 0; b0 < total; b0 += RT_BATCH) {
-    C r[RT_BATCH];
-#pragma unroll
-    for (int j = 0; j < RT_BATCH; ++j) {
-      const int f = b0 + j;
+    for (int f = 0; f < total; ++f) {
       const int t = f / per, i = f - t * per;
       const int q = tid + i * NTHR;
-      if (f < total && q < chunks) {
-        const int x = q >> log_cin, c = q & (cin - 1);
-        r[j] = gload<W, NC>((t == 0 ? src0 : src1) + (uint64_t)x * row_stride +
-                            (unsigned)c * W);
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < RT_BATCH; ++j) {
-      const int f = b0 + j;
-      const int t = f / per, i = f - t * per;
-      const int q = tid + i * NTHR;
-      if (f < total && q < chunks) {
+      if (q < chunks) {
         const int x = q >> log_cin, c = q & (cin - 1);
         const int X = REV ? (int)rev_bits((uint32_t)x, bx) : x;
         const int pc = c ^ ((X >> LOG_V) & mask);
-        sm[t * chunks + (X << log_cin) + pc] = r[j];
+        cp_async16(sm + t * chunks + (X << log_cin) + pc,
+                   (t == 0 ? src0 : src1) + (uint64_t)x * row_stride + (unsigned)c * 16);
+      }
+    }
+    cp_async_wait_all();
+  } else {
+#pragma unroll 1
+    for (int b0 = 0; b0 < total; b0 += RT_BATCH) {
+      C r[RT_BATCH];
+#pragma unroll
+      for (int j = 0; j < RT_BATCH; ++j) {
+        const int f = b0 + j;
+        const int t = f / per, i = f - t * per;
+        const int q = tid + i * NTHR;
+        if (f < total && q < chunks) {
+          const int x = q >> log_cin, c = q & (cin - 1);
+          r[j] = gload<W, NC>((t == 0 ? src0 : src1) + (uint64_t)x * row_stride +
+                              (unsigned)c * W);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < RT_BATCH; ++j) {
+        const int f = b0 + j;
+        const int t = f / per, i = f - t * per;
+        const int q = tid + i * NTHR;
+        if (f < total && q < chunks) {
+          const int x = q >> log_cin, c = q & (cin - 1);
+          const int X = REV ? (int)rev_bits((uint32_t)x, bx) : x;
+          const int pc = c ^ ((X >> LOG_V) & mask);
+          sm[t * chunks + (X << log_cin) + pc] = r[j];
+        }
       }
     }
   }
