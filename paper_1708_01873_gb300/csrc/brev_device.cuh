@@ -164,30 +164,18 @@ template <> struct ChunkT<4> { using type = uint32_t; };
 template <> struct ChunkT<2> { using type = uint16_t; };
 template <> struct ChunkT<1> { using type = uint8_t; };
 
-// Global loads.  NC: the source is read-only for the whole kernel
-// (out-of-place), so the non-coherent path is legal.  L1::no_allocate:
-// every byte is read once, keep it out of L1.
+// Global loads of the element-wide path (W = E < 16, pointers not 16-byte
+// aligned; 16-byte chunks go by asynchronous copies).  NC: the source is
+// read-only for the whole kernel (out-of-place), so the non-coherent path
+// is legal.
 template <int W, bool NC>
 __device__ __forceinline__ typename ChunkT<W>::type gload(const char* p) {
-  if constexpr (W == 16) {
-    uint4 r;
-    if constexpr (NC) {
-      asm("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
-          : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-          : "l"(p));
-    } else {
-      asm volatile("ld.global.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
-                   : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-                   : "l"(p));
-    }
-    return r;
+  static_assert(W < 16, "16-byte chunks are staged by cp.async");
+  using C = typename ChunkT<W>::type;
+  if constexpr (NC) {
+    return __ldg(reinterpret_cast<const C*>(p));
   } else {
-    using C = typename ChunkT<W>::type;
-    if constexpr (NC) {
-      return __ldg(reinterpret_cast<const C*>(p));
-    } else {
-      return *reinterpret_cast<const C*>(p);
-    }
+    return *reinterpret_cast<const C*>(p);
   }
 }
 
