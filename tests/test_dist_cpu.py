@@ -80,3 +80,25 @@ def test_reference_arm_under_torchrun_prints_once():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["value"] > 0 and d["n_gpus"] == 2
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+    # the same config object as the GPU arm's line (its sample is in cpu_baseline)
+    sys.path.insert(0, ROOT)
+    import bench
+    assert d["config"] == bench.sweep_config(28, "u32,f32,c64,c128", 2, None)
+    assert "bounded sample" in d["cpu_baseline"]["sample"]
+
+
+def test_sweep_config_counts():
+    """The sweep's reported size against a closed form: every k = 10..28 of
+    4 + 4 + 8 + 16 bytes per element, read and written, out of place and in
+    place -- 2 * 2 * (2^29 - 2^10) * 32 bytes in 152 points."""
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.sweep_config(28, "u32,f32,c64,c128", 1, 129)
+    assert c["points_per_step"] == 152
+    assert c["bytes_per_step"] == 2 * 2 * ((1 << 29) - (1 << 10)) * 32 == 68719345664
+    assert "64 GiB moved per step" in c["l2"] and "L2 = 129 MiB" in c["l2"]
+    assert c["parallelism"] == "1 GPU"
+    small = bench.sweep_config(14, "c128", 4, 129)
+    assert small["points_per_step"] == 2 * 5
+    assert small["bytes_per_step"] == 2 * 2 * ((1 << 15) - (1 << 10)) * 16
+    assert "can stay in L2" in small["l2"] and small["parallelism"] == "replicas x4"
