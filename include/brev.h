@@ -24,8 +24,13 @@
  *     return; the caller synchronises.  Only brev_autotune and
  *     brev_permute_host (see there) block the calling thread.
  *   - The caller owns every data buffer.  The library owns only its small
- *     device workspaces (batch descriptors, host-path staging), plans and
- *     the tuning table.
+ *     device workspaces (batch descriptors, ticket counters, host-path
+ *     staging), plans and the tuning table.  Workspaces are stream-ordered
+ *     allocations from a memory pool the library creates per device on
+ *     first use; it keeps up to 32 MiB reserved across synchronisations
+ *     (so a call right after a synchronise does not map memory again) and
+ *     lives until the process exits.  The device's default memory pool is
+ *     not touched.
  *   - Every call returns a brev_status.  On failure nothing was enqueued
  *     (except for BREV_ERR_CUDA raised by the launch itself), and
  *     brev_last_error() returns a message for the calling thread.
