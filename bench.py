@@ -696,8 +696,12 @@ def bench_batched(torch, brev, inputs, device, stream, sampler, reduce_max, barr
 
 def bench_e2e(torch, brev, inputs, pts, seq, steps, stream, sampler, reduce_max, barrier,
               ws):
-    """The sweep through brev_permute_host: pinned host input copied in,
-    permuted, result copied back, every point every step."""
+    """The sweep through brev_permute_host, every point every step, timed on
+    the host clock around the calls (each returns with its result in host
+    memory).  The buffers are page-locked, so the tile kernel reads each
+    input from host memory and writes each result to host memory over
+    NVLink-C2C: every step moves all inputs host -> device and all results
+    device -> host, with no device copy in between."""
     L = brev.lib()
     sh = stream.cuda_stream
     kinds = {}
@@ -735,7 +739,9 @@ def bench_e2e(torch, brev, inputs, pts, seq, steps, stream, sampler, reduce_max,
     step_bytes = sum(p["bytes"] for p, _ in seq)
     return {"value": round(ws * step_bytes * steps / el / 1e9, 1), "unit": "GB/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d, "steps": steps,
-            "api": "brev_permute_host (pinned host buffers; H2D + permute + D2H per point)"}
+            "api": "brev_permute_host on page-locked host buffers: the kernel reads each "
+                   "input from and writes each result to host memory over NVLink-C2C, "
+                   "every point every step, host clock around the calls"}
 
 
 # --------------------------------------------------------- CPU baseline --
