@@ -182,16 +182,58 @@ __device__ __forceinline__ void dit_first_pass(uint4* sm0, int nt, uint32_t conj
   }
 }
 
-// Stages s0+1 .. s0+R (R <= 3) on every output row of a staged tile, in
-// registers: each thread takes groups of 2^R elements of one shared-memory
-// column, X = base + j + t 2^s0 (t < 2^R), which those R stages combine only
-// among themselves (the radix-2^R view of R consecutive radix-2 stages).
-// Forward twiddles; imaginary parts have their sign flipped by conj_out on
-// storing.
+// The butterflies of one group of the second pass, v holding the elements
+// X = base + j + t 2^S0 (t < 2^R) of one output row: stage s = S0 + r + 1
+// pairs t and t + 2^r with w = exp(-2 pi i jj / 2^s), jj = (j + t 2^S0) mod
+// 2^(s-1).  For a group whose j is known at compile time (J >= 0) every
+// twiddle that is a whole number of eighth turns (8 jj divisible by 2^s)
+// takes butterfly_const's form -- w = 1 and -i need no product -- and the
+// others the table; J = -1 reads every twiddle from the table.
+template <class G, int R, int S0, int J, class T>
+__device__ __forceinline__ void dit_group(T* v, int j, const T* tw) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int s = S0 + r + 1;
+    const int hmask = (1 << (s - 1)) - 1;
+#pragma unroll
+    for (int t = 0; t < (1 << R); ++t) {
+      if (t & (1 << r)) continue;
+      T& a = v[t];
+      T& b = v[t + (1 << r)];
+      if constexpr (J >= 0) {
+        const int jc = (J + (t << S0)) & hmask;  // folds to a constant once unrolled
+        if (((jc << 3) & ((1 << s) - 1)) == 0) {
+          switch ((jc << 3) >> s) {  // eighth turns
+            case 0: butterfly_const<T, 3, 0>(a, b); break;
+            case 1: butterfly_const<T, 3, 1>(a, b); break;
+            case 2: butterfly_const<T, 3, 2>(a, b); break;
+            default: butterfly_const<T, 3, 3>(a, b); break;
+          }
+          continue;
+        }
+      }
+      const int jj = (j + (t << S0)) & hmask;
+      butterfly(a, b, tw[jj << (G::BX - s)]);
+    }
+  }
+}
+
+// Stages 4 .. 3 + R (R <= 3) on every output row of a staged tile, in
+// registers, after the first pass took stages 1..3 (rows hold at most 2^6
+// elements, so this is the last pass): each thread takes groups of 2^R
+// elements of one shared-memory column, X = base + j + t 2^3 (t < 2^R),
+// which those R stages combine only among themselves (the radix-2^R view of
+// R consecutive radix-2 stages).  j is the same for the 32 lanes of a warp
+// (they take consecutive columns z of one group row when BZ >= 5), so the
+// branch to the groups with j = 0 and j = 4 -- whose twiddles are all or
+// mostly 1, -i and eighth turns -- does not diverge.  Forward twiddles;
+// imaginary parts have their sign flipped by conj_out on storing.
 template <class G, int NTHR, int R>
-__device__ __forceinline__ void dit_pass(uint4* sm0, int nt, int s0, uint32_t conj_out,
+__device__ __forceinline__ void dit_pass(uint4* sm0, int nt, uint32_t conj_out,
                                          const typename Cplx<G::E>::T* tw) {
+  static_assert(G::BX <= 6, "at most two passes: rows of at most 2^6 elements");
   using T = typename Cplx<G::E>::T;
+  constexpr int S0 = 3;
   constexpr int GN = 1 << R;
   constexpr int LOG_GROUPS = G::BX + G::BZ - R;
   for (int gt = threadIdx.x; gt < (nt << LOG_GROUPS); gt += NTHR) {
@@ -199,33 +241,26 @@ __device__ __forceinline__ void dit_pass(uint4* sm0, int nt, int s0, uint32_t co
     const int g = gt & ((1 << LOG_GROUPS) - 1);
     const int z = g & ((1 << G::BZ) - 1);
     const int q = g >> G::BZ;
-    const int j = q & ((1 << s0) - 1);
-    const int base = (q >> s0) << (s0 + R);
+    const int j = q & ((1 << S0) - 1);
+    const int base = (q >> S0) << (S0 + R);
     T v[GN];
 #pragma unroll
-    for (int t = 0; t < GN; ++t) v[t] = *tile_elem<G>(sm, base + j + (t << s0), z);
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int s = s0 + r + 1;
-      const int hmask = (1 << (s - 1)) - 1;
-#pragma unroll
-      for (int t = 0; t < GN; ++t) {
-        if (t & (1 << r)) continue;
-        const int jj = (j + (t << s0)) & hmask;
-        butterfly(v[t], v[t + (1 << r)], tw[jj << (G::BX - s)]);
-      }
-    }
+    for (int t = 0; t < GN; ++t) v[t] = *tile_elem<G>(sm, base + j + (t << S0), z);
+    if (j == 0) dit_group<G, R, S0, 0>(v, j, tw);
+    else if (j == 4) dit_group<G, R, S0, 4>(v, j, tw);
+    else dit_group<G, R, S0, -1>(v, j, tw);
 #pragma unroll
     for (int t = 0; t < GN; ++t) {
       v[t].y = flip_sign(v[t].y, conj_out);
-      *tile_elem<G>(sm, base + j + (t << s0), z) = v[t];
+      *tile_elem<G>(sm, base + j + (t << S0), z) = v[t];
     }
   }
 }
 
-// Stages 1..S on every output row of a staged tile (columns of sm), three
-// at a time: the first pass with compile-time twiddles, later ones from the
-// table.  The butterflies are always the forward ones.  The inverse stages
+// Stages 1..S on every output row of a staged tile (columns of sm): the
+// first pass takes stages 1..3 with compile-time twiddles, the second
+// stages 4..S (S <= 6), from the table except where they are whole eighth
+// turns.  The butterflies are always the forward ones.  The inverse stages
 // (conjugate twiddles) are conj(forward(conj(x))) exactly -- every operation
 // of the butterflies is odd in the imaginary parts and rounding to nearest
 // is symmetric -- so the first pass flips the sign of the imaginary parts it
@@ -241,14 +276,11 @@ __device__ __forceinline__ void dit_stages(uint4* sm, int nt, int S, int inverse
   else if (R0 == 2) dit_first_pass<G, NTHR, 2>(sm, nt, conj, conj_out0);
   else dit_first_pass<G, NTHR, 1>(sm, nt, conj, conj_out0);
   __syncthreads();
-  int s0 = R0;
-  while (s0 < S) {
-    const int R = S - s0 >= 3 ? 3 : S - s0;
-    const uint32_t conj_out = s0 + R == S ? conj : 0u;
-    if (R == 3) dit_pass<G, NTHR, 3>(sm, nt, s0, conj_out, tw);
-    else if (R == 2) dit_pass<G, NTHR, 2>(sm, nt, s0, conj_out, tw);
-    else dit_pass<G, NTHR, 1>(sm, nt, s0, conj_out, tw);
-    s0 += R;
+  if (S > 3) {  // S <= BX <= 6: the second pass takes the rest, stages 4..S
+    const int R = S - 3;
+    if (R == 3) dit_pass<G, NTHR, 3>(sm, nt, conj, tw);
+    else if (R == 2) dit_pass<G, NTHR, 2>(sm, nt, conj, tw);
+    else dit_pass<G, NTHR, 1>(sm, nt, conj, tw);
     __syncthreads();
   }
 }

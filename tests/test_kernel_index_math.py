@@ -854,7 +854,14 @@ def test_fused_fft_multiply_add_butterflies():
                             for t in range(1 << R):
                                 if t & (1 << r):
                                     continue
-                                w = table[((j + (t << s0)) & hmask) << (B - s)]
+                                jj = (j + (t << s0)) & hmask
+                                if j in (0, 4) and (jj * 8) % (1 << s) == 0:
+                                    # dit_group<J = 0, 4>: whole eighth turns take
+                                    # butterfly_const's compile-time form
+                                    v[t], v[t + (1 << r)] = _bfly_const(
+                                        v[t], v[t + (1 << r)], 3, (jj * 8) >> s)
+                                    continue
+                                w = table[jj << (B - s)]
                                 v[t], v[t + (1 << r)] = _bfly_multiply_add(v[t], v[t + (1 << r)],
                                                                            w)
                         for X, val in zip(Xs, v):
