@@ -6,8 +6,8 @@ binding never import it; the two share no code.
 
 The arithmetic lives in ``oracle.c`` (plain C): the definition of the
 permutation from the paper's Introduction (element i moves to rev_k(i); the
-n = 8 worked example) and the pair-swap loop of Listing 1.  This module only
-compiles that file with gcc and marshals numpy buffers into it.
+n = 8 worked example), in place applied to a copy of the input.  This module
+only compiles that file with gcc and marshals numpy buffers into it.
 
 Pins that tie the oracle to the paper (worked example, brute force, the
 involution, the recursive even-odd definition, the XOR induction, the swap

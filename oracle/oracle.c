@@ -4,8 +4,8 @@
  * builtins, no tables, nothing shared with the GPU library.
  *
  * Every function is the plain definition from the Introduction of the paper
- * (element i moves to rev_k(i), worked example for n = 8) or the swap loop
- * of Listing 1.  No blocking, tiling or reordering is done here.
+ * (element i moves to rev_k(i), worked example for n = 8).  No blocking,
+ * tiling or reordering is done here.
  */
 #include "oracle.h"
 
@@ -52,30 +52,24 @@ int oracle_brev_oop(void *dst, const void *src, int k, int elem_bytes)
     return 0;
 }
 
-/* Listing 1: in-place by swapping each unique pair (i, rev(i)) once; the
- * comparison i < rev(i) stops a pair from being swapped back.  Listing 1
- * skips i = 0 and i = n-1 because both are their own reverse; visiting
- * them here is harmless (the comparison is false), so the loop runs over
- * every index, which also makes k = 0 and k = 1 plain identities. */
+/* In place (Introduction: the same map, with the result in the input's
+ * buffer): the definition applied to a copy of the input.  k = 0 and k = 1
+ * are identities like every other size, with no special case. */
 int oracle_brev_inplace(void *v, int k, int elem_bytes)
 {
-    uint64_t n, i, r;
-    unsigned char tmp[ORACLE_MAX_ELEM];
-    unsigned char *p = (unsigned char *)v;
+    uint64_t bytes;
+    void *copy;
+    int rc;
     if (bad_args(k, elem_bytes) || !v)
         return -1;
-    n = (uint64_t)1 << k;
-    for (i = 0; i < n; ++i) {
-        r = oracle_rev_bits(i, k);
-        if (i < r) {
-            unsigned char *a = p + i * (uint64_t)elem_bytes;
-            unsigned char *b = p + r * (uint64_t)elem_bytes;
-            memcpy(tmp, a, (size_t)elem_bytes);
-            memcpy(a, b, (size_t)elem_bytes);
-            memcpy(b, tmp, (size_t)elem_bytes);
-        }
-    }
-    return 0;
+    bytes = ((uint64_t)1 << k) * (uint64_t)elem_bytes;
+    copy = malloc((size_t)bytes);
+    if (!copy)
+        return -1;
+    memcpy(copy, v, (size_t)bytes);
+    rc = oracle_brev_oop(v, copy, k, elem_bytes);
+    free(copy);
+    return rc;
 }
 
 struct oop_slice {

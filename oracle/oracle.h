@@ -33,8 +33,9 @@ uint64_t oracle_rev_bits(uint64_t i, int k);
  * Returns 0, or -1 on a bad argument. */
 int oracle_brev_oop(void *dst, const void *src, int k, int elem_bytes);
 
-/* In-place permutation by pair swaps (Listing 1: visit every index, swap
- * v[i] with v[rev_k(i)] only when i < rev_k(i)).  Returns 0 or -1. */
+/* In-place permutation: the definition (v[rev_k(i)] = old v[i]) applied to
+ * a copy of the input.  Returns 0, or -1 on a bad argument or when the copy
+ * cannot be allocated. */
 int oracle_brev_inplace(void *v, int k, int elem_bytes);
 
 /* The out-of-place definition again with the index range split over

@@ -186,6 +186,19 @@ class SwapWithoutComparison(_Mutant):
         return buf
 
 
+class InPlaceWithoutCopy(_Mutant):
+    """The in-place definition applied to the buffer itself, without a copy
+    of the input: later reads see elements already overwritten."""
+
+    def inplace(self, buf, k, E):
+        n = 1 << k
+        a = buf.reshape(n, E)
+        r = self.rev_vec(np.arange(n, dtype=np.uint64), k).astype(np.int64)
+        for i in range(n):
+            a[r[i]] = a[i]
+        return buf
+
+
 class HalvesSwapped(_Mutant):
     """rev(x y) computed as rev(x) rev(y) (operands of the concatenation
     transposed)."""
@@ -199,7 +212,7 @@ class HalvesSwapped(_Mutant):
 
 @pytest.mark.parametrize("mutant", [RotateNotReverse, DroppedLowBit, OffByOneWidth,
                                     PartialElementCopy, SwapWithoutComparison,
-                                    HalvesSwapped])
+                                    InPlaceWithoutCopy, HalvesSwapped])
 def test_pins_catch_planted_mistake(mutant):
     m = mutant()
     fast = [
