@@ -82,6 +82,14 @@ static cudaError_t workspace_pool(cudaMemPool_t* out) {
   std::lock_guard<std::mutex> lk(g_mu);
   if ((int)g_ws_pools.size() <= dev) g_ws_pools.resize(dev + 1, nullptr);
   if (!g_ws_pools[dev]) {
+    // the first stream-ordered allocation may come inside a stream capture:
+    // creating the pool is not a stream operation, so it may run there
+    cudaStreamCaptureMode mode = cudaStreamCaptureModeRelaxed;
+    cudaThreadExchangeStreamCaptureMode(&mode);
+    struct Restore {
+      cudaStreamCaptureMode m;
+      ~Restore() { cudaThreadExchangeStreamCaptureMode(&m); }
+    } restore{mode};
     cudaMemPoolProps props;
     memset(&props, 0, sizeof(props));
     props.allocType = cudaMemAllocationTypePinned;
@@ -284,11 +292,25 @@ static double g_tuned_gbs[5][2][BREV_MAX_LOG2N + 1];
 // tuned batched tile exponent + 1 per element size and k (0: not tuned);
 // read without the lock on every array of a batched call
 static std::atomic<int8_t> g_tuned_batched[5][BREV_MAX_LOG2N + 1];
+// tuned stage count of a batch whose largest stage is an array (k, E) (0: not tuned)
+static std::atomic<int8_t> g_tuned_batched_stages[5][BREV_MAX_LOG2N + 1];
+// tuned staging of the array's tile rows + 1 (0: not tuned)
+static std::atomic<int8_t> g_tuned_batched_copy[5][BREV_MAX_LOG2N + 1];
 static double g_tuned_batched_gbs[5][BREV_MAX_LOG2N + 1];
 
 int tuned_batched_b(int k, int E) {
   if (k < 0 || k > BREV_MAX_LOG2N || !valid_E(E)) return -1;
   return (int)g_tuned_batched[e_index(E)][k].load(std::memory_order_relaxed) - 1;
+}
+
+int tuned_batched_stages(int k, int E) {
+  if (k < 0 || k > BREV_MAX_LOG2N || !valid_E(E)) return 0;
+  return (int)g_tuned_batched_stages[e_index(E)][k].load(std::memory_order_relaxed);
+}
+
+int tuned_batched_copy(int k, int E) {
+  if (k < 0 || k > BREV_MAX_LOG2N || !valid_E(E)) return -1;
+  return (int)g_tuned_batched_copy[e_index(E)][k].load(std::memory_order_relaxed) - 1;
 }
 
 struct Choice {
@@ -657,6 +679,10 @@ void brev_reset_tuning(void) {
   memset(g_tuned_gbs, 0, sizeof(g_tuned_gbs));
   for (auto& row : g_tuned_batched)
     for (auto& v : row) v.store(0, std::memory_order_relaxed);
+  for (auto& row : g_tuned_batched_stages)
+    for (auto& v : row) v.store(0, std::memory_order_relaxed);
+  for (auto& row : g_tuned_batched_copy)
+    for (auto& v : row) v.store(0, std::memory_order_relaxed);
   memset(g_tuned_batched_gbs, 0, sizeof(g_tuned_batched_gbs));
 }
 
@@ -697,8 +723,13 @@ static brev_status write_cache(const char* path) {
     for (int k = 0; k <= BREV_MAX_LOG2N; ++k) {
       const int v = g_tuned_batched[ei][k].load(std::memory_order_relaxed);
       if (v <= 0) continue;
-      fprintf(f, "%s\n  {\"elem_bytes\": %d, \"log2n\": %d, \"batched_b\": %d, \"gbs\": %.1f}",
-              first ? "" : ",", Es[ei], k, v - 1, g_tuned_batched_gbs[ei][k]);
+      fprintf(f,
+              "%s\n  {\"elem_bytes\": %d, \"log2n\": %d, \"batched_b\": %d, "
+              "\"batched_stages\": %d, \"batched_copy\": %d, \"gbs\": %.1f}",
+              first ? "" : ",", Es[ei], k, v - 1,
+              (int)g_tuned_batched_stages[ei][k].load(std::memory_order_relaxed),
+              (int)g_tuned_batched_copy[ei][k].load(std::memory_order_relaxed) - 1,
+              g_tuned_batched_gbs[ei][k]);
       first = false;
     }
   fprintf(f, "\n]}\n");
@@ -766,6 +797,17 @@ brev_status brev_load_tune_cache(const char* path) {
         const int nc = batched_candidates((int)k, (int)E, cand, &def);
         if (std::find(cand, cand + nc, (int)bb) != cand + nc) {
           g_tuned_batched[e_index((int)E)][k].store((int8_t)(bb + 1), std::memory_order_relaxed);
+          long ns = 0;
+          int sc[8];
+          const int nsc = batched_stage_candidates((int)k, (int)E, (int)bb, sc);
+          if (json_int(p, q, "batched_stages", &ns) &&
+              std::find(sc, sc + nsc, (int)ns) != sc + nsc)
+            g_tuned_batched_stages[e_index((int)E)][k].store((int8_t)ns,
+                                                             std::memory_order_relaxed);
+          long cp = -1;
+          if (bb > 0 && json_int(p, q, "batched_copy", &cp) && (cp == 0 || cp == 1))
+            g_tuned_batched_copy[e_index((int)E)][k].store((int8_t)(cp + 1),
+                                                           std::memory_order_relaxed);
           ++loaded;
         }
       }
@@ -791,71 +833,179 @@ brev_status brev_load_tune_cache(const char* path) {
   return BREV_OK;
 }
 
-// Batched tile exponent per k: time every candidate b on a batch of equal
-// arrays of 2^k elements (up to 4096 of them, about 256 MiB in all),
-// L2 flushed before each launch, and keep the fastest unless the built-in
-// choice is within 3 %.
-static brev_status autotune_batched(int k_min, int k_max, int E, cudaStream_t st, void* fl,
-                                    size_t flush_bytes, cudaEvent_t e0, cudaEvent_t e1) {
-  constexpr uint64_t BUDGET = 256ull << 20;
+// Tuning runs print every candidate's time to stderr when BREV_TUNE_VERBOSE
+// is set (the cache keeps only the winners).
+static bool tune_verbose() {
+  const char* v = getenv("BREV_TUNE_VERBOSE");
+  return v && *v && strcmp(v, "0") != 0;
+}
+
+// Batched tile exponent and stage count per k: time every candidate
+// (b, stages) on a batch of equal arrays of 2^k elements (up to 4096 of
+// them, at most `budget` bytes in all), R launches back to back, and keep
+// the fastest unless the built-in choice is within 3 %.  A batch larger
+// than L2 is read from HBM at every launch; smaller batches (short arrays)
+// run as they would in a caller's back-to-back use.
+static brev_status autotune_batched(int k_min, int k_max, int E, cudaStream_t st,
+                                    uint64_t budget, cudaEvent_t e0, cudaEvent_t e1) {
   constexpr int MAX_ARRAYS = 4096;
+  constexpr int R = 4;
   void* buf = nullptr;
-  cudaError_t e = cudaMalloc(&buf, BUDGET);
+  cudaError_t e = cudaMalloc(&buf, budget);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return set_error(BREV_ERR_OOM, "batched autotune buffer: %s", cudaGetErrorString(e));
   }
-  cudaMemsetAsync(buf, 0x3C, BUDGET, st);
+  cudaMemsetAsync(buf, 0x3C, budget, st);
   brev_status result = BREV_OK;
   std::vector<BatchItem> items;
   for (int k = std::max(k_min, 2); k <= k_max && result == BREV_OK; ++k) {
     int cand[8], def = -1;
     const int nc = batched_candidates(k, E, cand, &def);
-    if (nc < 2 || def < 0) continue;  // nothing to choose
+    if (nc < 1 || def < 0) continue;
     const uint64_t bytes = (uint64_t)E << k;
-    const int count = (int)std::min<uint64_t>(MAX_ARRAYS, BUDGET / bytes);
+    const int count = (int)std::min<uint64_t>(MAX_ARRAYS, budget / bytes);
     if (count < 1) continue;
     items.assign(count, BatchItem{});
     for (int i = 0; i < count; ++i) items[i] = BatchItem{(char*)buf + (uint64_t)i * bytes, k, E};
-    double best = 1e30, def_med = 0;
-    int best_b = -1;
+    double best = 1e30, def_ms = 0;
+    int best_b = -1, best_s = 0, best_c = -1;
     for (int c = 0; c < nc && result == BREV_OK; ++c) {
-      std::vector<float> ms;
-      for (int r = 0; r < 9 && result == BREV_OK; ++r) {
-        cudaMemsetAsync(fl, r & 0xFF, flush_bytes, st);
-        cudaEventRecord(e0, st);
-        result = batched_launch_forced(items.data(), count, cand[c], st);
-        cudaEventRecord(e1, st);
-        if (cudaEventSynchronize(e1) != cudaSuccess) {
-          result = cuda_error(cudaGetLastError(), "batched autotune timing");
-          break;
+      int sc[8];
+      const int ns = batched_stage_candidates(k, E, cand[c], sc);
+      // (stages, copy) candidates: the built-in choice (0, -1) first, then
+      // every stage count with either staging (whole arrays: bulk only)
+      const int ncopy = cand[c] > 0 ? 2 : 1;
+      for (int si = -1; si < ns * ncopy && result == BREV_OK; ++si) {
+        const int stages = si < 0 ? 0 : sc[si / ncopy];
+        const int copy = si < 0 ? -1 : (cand[c] > 0 ? si % ncopy : 0);
+        double ms_best = 1e30;
+        for (int r = 0; r < 2 + 3 && result == BREV_OK; ++r) {
+          if (r >= 2) cudaEventRecord(e0, st);
+          for (int j = 0; j < (r >= 2 ? R : 1) && result == BREV_OK; ++j)
+            result = batched_launch_forced(items.data(), count, cand[c], stages, copy, st);
+          if (result != BREV_OK) break;
+          if (r < 2) continue;  // warm-up
+          cudaEventRecord(e1, st);
+          if (cudaEventSynchronize(e1) != cudaSuccess) {
+            result = cuda_error(cudaGetLastError(), "batched autotune timing");
+            break;
+          }
+          float m = 0;
+          cudaEventElapsedTime(&m, e0, e1);
+          ms_best = std::min(ms_best, (double)m / R);
         }
-        float m = 0;
-        cudaEventElapsedTime(&m, e0, e1);
-        if (r >= 2) ms.push_back(m);  // two warm-up runs
-      }
-      if (result != BREV_OK) break;
-      std::sort(ms.begin(), ms.end());
-      const double med = ms[ms.size() / 2];
-      if (cand[c] == def) def_med = med;
-      if (med < best) {
-        best = med;
-        best_b = cand[c];
+        if (result != BREV_OK) break;
+        if (tune_verbose())
+          fprintf(stderr,
+                  "brev tune batched E=%d k=%d count=%d b=%d stages=%d copy=%d: %.4f ms %.1f GB/s\n",
+                  E, k, count, cand[c], stages, copy, ms_best,
+                  2.0 * (double)bytes * count / (ms_best * 1e-3) / 1e9);
+        if (cand[c] == def && stages == 0 && copy < 0) def_ms = ms_best;
+        if (ms_best < best) {
+          best = ms_best;
+          best_b = cand[c];
+          best_s = stages;
+          best_c = copy;
+        }
       }
     }
     if (result != BREV_OK) break;
-    if (def_med > 0 && best > 0.97 * def_med) {
-      best = def_med;
+    if (def_ms > 0 && best > 0.97 * def_ms) {
+      best = def_ms;
       best_b = def;
+      best_s = 0;
+      best_c = -1;
     }
     if (best_b >= 0) {
       g_tuned_batched[e_index(E)][k].store((int8_t)(best_b + 1), std::memory_order_relaxed);
+      g_tuned_batched_stages[e_index(E)][k].store((int8_t)best_s, std::memory_order_relaxed);
+      g_tuned_batched_copy[e_index(E)][k].store((int8_t)(best_c + 1), std::memory_order_relaxed);
       g_tuned_batched_gbs[e_index(E)][k] = 2.0 * (double)bytes * count / (best * 1e-3) / 1e9;
     }
   }
   cudaStreamSynchronize(st);
   cudaFree(buf);
   return result;
+}
+
+// Time one shape back to back: a CUDA graph of R launches over buffer sets
+// carved from `pool` whose footprint together exceeds 3x L2 (each launch
+// then reads its source from HBM, as in a caller's stream of permutations
+// of different arrays), replayed three times after a warm-up; returns the
+// best replay's time per launch in ms, or a negative value on error.
+static double time_shape_b2b(const Choice& c, int k, int E, bool inplace, char* pool,
+                             uint64_t pool_bytes, uint64_t l2, cudaStream_t st, cudaEvent_t e0,
+                             cudaEvent_t e1, brev_status* result) {
+  const uint64_t bytes = (uint64_t)E << k;
+  const uint64_t foot = inplace ? bytes : 2 * bytes;
+  const uint64_t M = std::max<uint64_t>(
+      1, std::min<uint64_t>(pool_bytes / foot, (3 * l2 + foot - 1) / foot));
+  const double est_s = 2.0 * (double)bytes / 6.5e12 + 1.5e-6;
+  const int R = (int)std::max(4.0, std::min(256.0, std::ceil(1e-3 / est_s)));
+  auto set = [&](int r, char** dst, char** src) {
+    if (M == 1 && !inplace) {  // one set: ping-pong between its halves
+      char* a = pool;
+      char* b = pool + bytes;
+      *src = (r & 1) ? b : a;
+      *dst = (r & 1) ? a : b;
+      return;
+    }
+    char* base = pool + (uint64_t)(r % M) * foot;
+    *src = base;
+    *dst = inplace ? base : base + bytes;
+  };
+  char *d0, *s0;
+  set(0, &d0, &s0);
+  *result = launch_choice(c, d0, s0, k, E, st);  // shared-memory limits and pools set up
+  if (*result != BREV_OK) return -1;
+  if (cudaStreamSynchronize(st) != cudaSuccess) {
+    *result = cuda_error(cudaGetLastError(), "autotune warm-up");
+    return -1;
+  }
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    *result = cuda_error(e, "autotune capture");
+    return -1;
+  }
+  brev_status s = BREV_OK;
+  for (int r = 0; r < R && s == BREV_OK; ++r) {
+    char *d, *src;
+    set(r, &d, &src);
+    s = launch_choice(c, d, src, k, E, st);
+  }
+  e = cudaStreamEndCapture(st, &g);
+  if (s != BREV_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    *result = s != BREV_OK ? s : cuda_error(e, "autotune capture");
+    return -1;
+  }
+  note_launch_adjust(-(int64_t)R);  // counted at each replay below
+  e = cudaGraphInstantiate(&ge, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    *result = cuda_error(e, "autotune graph");
+    return -1;
+  }
+  double best = 1e30;
+  for (int rep = 0; rep < 4; ++rep) {
+    cudaEventRecord(e0, st);
+    e = cudaGraphLaunch(ge, st);
+    cudaEventRecord(e1, st);
+    if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+      cudaGraphExecDestroy(ge);
+      *result = cuda_error(e != cudaSuccess ? e : cudaGetLastError(), "autotune replay");
+      return -1;
+    }
+    note_launch(R);
+    float m = 0;
+    cudaEventElapsedTime(&m, e0, e1);
+    if (rep > 0) best = std::min(best, (double)m / R);  // the first replay warms up
+  }
+  cudaGraphExecDestroy(ge);
+  return best;
 }
 
 brev_status brev_autotune(int k_min, int k_max, int elem_bytes, const char* cache_path) {
@@ -871,11 +1021,11 @@ brev_status brev_autotune(int k_min, int k_max, int elem_bytes, const char* cach
   int dev = 0, l2 = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
-  const size_t flush_bytes = std::max<size_t>(2ull * (size_t)l2, 64ull << 20);
-  void *a = nullptr, *b = nullptr, *fl = nullptr;
-  e = cudaMalloc(&a, max_bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&b, max_bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&fl, flush_bytes);
+  // one pool for the rotating buffer sets: the largest array out of place,
+  // or 4x L2, whichever is larger
+  const uint64_t pool_bytes = std::max<uint64_t>(2 * max_bytes, 4ull * (uint64_t)l2);
+  void* pool = nullptr;
+  e = cudaMalloc(&pool, pool_bytes);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -885,81 +1035,56 @@ brev_status brev_autotune(int k_min, int k_max, int elem_bytes, const char* cach
     result = set_error(BREV_ERR_OOM, "autotune buffers: %s", cudaGetErrorString(e));
   }
   if (result == BREV_OK) {
-    cudaMemsetAsync(a, 0x5A, max_bytes, st);
+    cudaMemsetAsync(pool, 0x5A, pool_bytes, st);
     for (int k = k_min; k <= k_max && result == BREV_OK; ++k) {
       if (k < 2 * b_min_for(E)) continue;
       const uint64_t bytes = (uint64_t)E << k;
-      const int reps = bytes >= (64ull << 20) ? 5 : 11;
       for (int ip = 0; ip < 2 && result == BREV_OK; ++ip) {
         int n = 0;
         const ShapeEntry* t = table_for(E, &n);
-        double best = 1e30, def_med = 0;
+        double best = 1e30, def_ms = 0;
         int bbx = 0, bbz = 0, bord = 0;
         const ShapeEntry* def = choose_default(k, E, ip != 0, true).entry;
-        for (int i = 0; i < n; ++i) {
-          if (t[i].E != E || t[i].W != 16 || t[i].kind != ip || t[i].bx + t[i].bz > k) continue;
-          Choice c{false, &t[i]};
-          void* dst = ip ? a : b;
-          std::vector<float> ms;
-          for (int r = 0; r < reps + 2 && result == BREV_OK; ++r) {
-            cudaMemsetAsync(fl, r & 0xFF, flush_bytes, st);  // evict the array from L2
-            cudaEventRecord(e0, st);
-            result = launch_choice(c, dst, a, k, E, st);
-            cudaEventRecord(e1, st);
-            if (cudaEventSynchronize(e1) != cudaSuccess) {
-              result = cuda_error(cudaGetLastError(), "autotune timing");
-              break;
-            }
-            float m = 0;
-            cudaEventElapsedTime(&m, e0, e1);
-            if (r >= 2) ms.push_back(m);  // two warm-up runs
-          }
-          if (result != BREV_OK) break;
-          std::sort(ms.begin(), ms.end());
-          const double med = ms[ms.size() / 2];
-          if (&t[i] == def) def_med = med;
-          if (med < best) {
-            best = med;
-            bbx = t[i].bx;
-            bbz = t[i].bz;
-            bord = t[i].order;
-          }
-        }
-        // in place: the TMA pipeline (order 2) for each of its tile exponents
+        // the tile kernels (orders 0 and 1), then in place the TMA pipeline
+        // (order 2) for each of its tile exponents
         int pb[8];
-        const int np = (ip && result == BREV_OK) ? pipeline_shapes(E, pb) : 0;
-        for (int i = 0; i < np && result == BREV_OK; ++i) {
-          if (!pipeline_shape_ok(k, E, pb[i])) continue;
-          Choice c{false, nullptr, pb[i]};
-          std::vector<float> ms;
-          for (int r = 0; r < reps + 2 && result == BREV_OK; ++r) {
-            cudaMemsetAsync(fl, r & 0xFF, flush_bytes, st);
-            cudaEventRecord(e0, st);
-            result = launch_choice(c, a, a, k, E, st);
-            cudaEventRecord(e1, st);
-            if (cudaEventSynchronize(e1) != cudaSuccess) {
-              result = cuda_error(cudaGetLastError(), "autotune timing");
-              break;
-            }
-            float m = 0;
-            cudaEventElapsedTime(&m, e0, e1);
-            if (r >= 2) ms.push_back(m);
+        const int np = ip ? pipeline_shapes(E, pb) : 0;
+        for (int i = 0; i < n + np && result == BREV_OK; ++i) {
+          Choice c{false, nullptr};
+          int cbx, cbz, cord;
+          if (i < n) {
+            if (t[i].E != E || t[i].W != 16 || t[i].kind != ip || t[i].bx + t[i].bz > k)
+              continue;
+            c.entry = &t[i];
+            cbx = t[i].bx;
+            cbz = t[i].bz;
+            cord = t[i].order;
+          } else {
+            if (!pipeline_shape_ok(k, E, pb[i - n])) continue;
+            c.pipe_b = pb[i - n];
+            cbx = cbz = pb[i - n];
+            cord = 2;
           }
+          const double ms = time_shape_b2b(c, k, E, ip != 0, (char*)pool, pool_bytes,
+                                           (uint64_t)l2, st, e0, e1, &result);
           if (result != BREV_OK) break;
-          std::sort(ms.begin(), ms.end());
-          const double med = ms[ms.size() / 2];
-          if (med < best) {
-            best = med;
-            bbx = bbz = pb[i];
-            bord = 2;
+          if (tune_verbose())
+            fprintf(stderr, "brev tune E=%d k=%d %s %dx%d order %d: %.5f ms %.1f GB/s\n", E, k,
+                    ip ? "in-place" : "out-of-place", cbx, cbz, cord, ms,
+                    2.0 * (double)bytes / (ms * 1e-3) / 1e9);
+          if (i < n && &t[i] == def) def_ms = ms;
+          if (ms < best) {
+            best = ms;
+            bbx = cbx;
+            bbz = cbz;
+            bord = cord;
           }
         }
         if (result != BREV_OK) break;
         // keep the built-in shape unless another one is clearly faster:
-        // small arrays are launch-latency bound and their timings differ
-        // by noise only
-        if (def && def_med > 0 && best > 0.97 * def_med) {
-          best = def_med;
+        // small arrays are launch-bound and their timings differ by noise
+        if (def && def_ms > 0 && best > 0.97 * def_ms) {
+          best = def_ms;
           bbx = def->bx;
           bbz = def->bz;
           bord = def->order;
@@ -974,14 +1099,17 @@ brev_status brev_autotune(int k_min, int k_max, int elem_bytes, const char* cach
       }
     }
   }
-  if (result == BREV_OK && (E == 4 || E == 8 || E == 16))
-    result = autotune_batched(k_min, std::min(k_max, 24), E, st, fl, flush_bytes, e0, e1);
+  if (result == BREV_OK && (E == 4 || E == 8 || E == 16)) {
+    cudaStreamSynchronize(st);
+    cudaFree(pool);
+    pool = nullptr;
+    result = autotune_batched(k_min, std::min(k_max, 24), E, st,
+                              std::max<uint64_t>(512ull << 20, 4ull * (uint64_t)l2), e0, e1);
+  }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   cudaStreamSynchronize(st);
-  if (a) cudaFree(a);
-  if (b) cudaFree(b);
-  if (fl) cudaFree(fl);
+  if (pool) cudaFree(pool);
   cudaStreamDestroy(st);
   if (result == BREV_OK && cache_path) result = write_cache(cache_path);
   return result;
@@ -1007,6 +1135,27 @@ brev_status brev_get_device_info(brev_device_info* out) {
 }
 
 uint64_t brev_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+brev_status brev_workspace_bytes(uint64_t* reserved, uint64_t* used) {
+  if (!reserved || !used) return set_error(BREV_ERR_INVALID_ARG, "NULL output");
+  *reserved = *used = 0;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+  cudaMemPool_t pool = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (dev < (int)g_ws_pools.size()) pool = g_ws_pools[dev];
+  }
+  if (!pool) return BREV_OK;
+  uint64_t r = 0, u = 0;  // the attributes are 64-bit byte counts
+  e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &r);
+  if (e == cudaSuccess) e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &u);
+  if (e != cudaSuccess) return cuda_error(e, "workspace pool attributes");
+  *reserved = (uint64_t)r;
+  *used = (uint64_t)u;
+  return BREV_OK;
+}
 
 const char* brev_status_string(brev_status s) {
   switch (s) {

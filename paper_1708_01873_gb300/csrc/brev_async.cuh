@@ -52,6 +52,16 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// Tie this thread's earlier per-thread asynchronous copies (cp.async) to
+// `bar`: the barrier's pending count rises by one now and falls by one
+// when those copies have landed, so the current phase cannot complete
+// before them.  Every thread that issued copies executes it before the
+// phase's last ordinary arrival.
+__device__ __forceinline__ void cp_async_mbar_arrive(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.shared::cta.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t done;
   asm volatile(

@@ -28,13 +28,18 @@ namespace brev {
 struct BatchDesc {
   char* ptr;
   unsigned long long first_ticket;  // tickets [first_ticket, first_ticket + tickets)
-  unsigned units;                   // work units of this array
+  unsigned units;                   // work units covered: [unit0, unit0 + units)
   unsigned grain;                   // units per ticket
   int k;                            // BATCH_BITREV: log2 n; BATCH_TRANSPOSE: log2 of the side
   int E;
   int b;                            // square tile exponent; 0 = whole array in one CTA
   int mode;                         // BATCH_BITREV or BATCH_TRANSPOSE
+  unsigned unit0;                   // first unit of the array this descriptor covers
+  int copy;                         // tile rows staged by BATCH_COPY_BULK or BATCH_COPY_CHUNKS
 };
+// An array's units may be spread over several consecutive descriptors with
+// different grains (finer tickets near the end of a batch).
+static_assert(sizeof(BatchDesc) == 48, "descriptor layout (the no-alloc scratch is sized by it)");
 // Descriptor modes: in-place bit reversal of 2^k elements (units: tile
 // pairs (y, rev y) then self-paired tiles), or in-place transposition of a
 // 2^k x 2^k matrix (units: tile pairs (tr, tc), tr < tc, and diagonal
@@ -43,6 +48,23 @@ struct BatchDesc {
 // (reversal vs identity).
 constexpr int BATCH_BITREV = 0;
 constexpr int BATCH_TRANSPOSE = 1;
+// How the producer warp stages a unit's tile rows: one bulk copy (TMA) per
+// row, or the row's 16-byte chunks spread over the warp's lanes as
+// per-thread asynchronous copies.  The bulk copy engine takes about one
+// request per 30 SM cycles whatever its size, so rows of 256 bytes or less
+// (4- and 8-byte elements) cap a batch at ~5.3-5.8 TB/s that way on GB300;
+// chunks have no per-row cost.  Whole small arrays (b = 0) always go as one
+// bulk copy.
+constexpr int BATCH_COPY_BULK = 0;
+constexpr int BATCH_COPY_CHUNKS = 1;
+
+// Built-in staging of an array's tile rows: chunks for rows narrower than
+// 512 bytes (where the bulk copy engine's per-request cost binds), bulk
+// copies otherwise.
+__host__ __device__ inline int batched_copy_default(int E, int b) {
+  return b > 0 && (E << b) < 512 ? BATCH_COPY_CHUNKS : BATCH_COPY_BULK;
+}
+
 
 constexpr int BATCH_THREADS = 256;
 #ifndef BREV_BATCHED_TICKET_BYTES
@@ -95,10 +117,14 @@ __device__ __forceinline__ int find_array(const BatchDesc* __restrict__ d, int c
 #define BREV_BATCHED_STORE_UNROLL 1
 #endif
 constexpr int BATCH_STORE_UNROLL = BREV_BATCHED_STORE_UNROLL;
+// Pipeline stages per CTA.  The resident serving kernel uses BATCH_STAGES;
+// the batched kernel takes its stage count at launch (2 .. BATCH_MAX_STAGES,
+// chosen per batch from the stage size, or tuned).
 #ifndef BREV_BATCHED_STAGES
 #define BREV_BATCHED_STAGES 2
 #endif
 constexpr int BATCH_STAGES = BREV_BATCHED_STAGES;
+constexpr int BATCH_MAX_STAGES = 6;
 
 // Unit staged in one pipeline stage.  nt: 2 = tile pair, 1 = self-paired
 // tile, 0 = small array staged whole, -1 = no unit.
@@ -195,6 +221,29 @@ __device__ __forceinline__ void issue_unit(const BatchDesc& d, unsigned u, Stage
   const uint32_t rowb = (uint32_t)d.E << b;
   const uint32_t pitch = padded_row_bytes(d.E, b);
   const int rows = 1 << b;
+  if (d.copy == BATCH_COPY_CHUNKS) {
+    // chunk q: tile t, row x, 16-byte chunk c (consecutive lanes take
+    // consecutive chunks of a row, so each warp instruction reads whole
+    // rows); the lanes' copies complete on `full`, then lane 0's arrival
+    // (which also publishes the unit's description) ends the phase's count
+    const int log_cpr = __ffs((int)(rowb >> 4)) - 1;  // rowb / 16 is a power of two
+    const int chunks = s.nt * (rows << log_cpr);
+    for (int q = lane; q < chunks; q += 32) {
+      const int c = q & ((1 << log_cpr) - 1);
+      const int tx = q >> log_cpr;
+      const int t = tx >> b, x = tx & (rows - 1);
+      const uint32_t X = s.rev ? rev_bits((uint32_t)x, b) : (uint32_t)x;
+      cp_async16(buf + (uint32_t)t * rows * pitch + X * pitch + (uint32_t)c * 16,
+                 (t ? s.r : s.a) + (uint64_t)x * s.stride + (uint32_t)c * 16);
+    }
+    cp_async_mbar_arrive(full);
+    __syncwarp();
+    if (lane == 0) {
+      *info = s;
+      mbar_arrive(full);
+    }
+    return;
+  }
   if (lane == 0) {
     *info = s;
     mbar_arrive_expect_tx(full, (uint32_t)s.nt * rows * rowb);
@@ -258,7 +307,7 @@ __device__ BREV_BATCHED_BODY_ATTR void store_staged_unit(const unsigned char* sm
 }
 
 // Warps 0..7 store (consumers, threads 0..255); warp 8 is the producer.
-// Stage p serves units p, p + S, p + 2S, ... (S = BATCH_STAGES).  full[p]
+// Stage p serves units p, p + S, p + 2S, ... (S = `stages`).  full[p]
 // completes when the unit's copies have landed (one producer arrival plus
 // the bytes); empty[p] completes when all 8 consumer warps have read the
 // stage.  No block-wide barrier after the set-up: each consumer warp moves
@@ -271,13 +320,14 @@ constexpr int BATCH_BLOCK = BATCH_THREADS + 32;
 __global__ void __launch_bounds__(BATCH_BLOCK, BREV_BATCHED_MIN_CTAS)
     k_batched(const BatchDesc* __restrict__ desc, int count, const BatchDesc one,
               unsigned long long tickets, unsigned long long* ticket_ctr,
-              unsigned stage_bytes) {
+              unsigned stage_bytes, int stages) {
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ __align__(8) uint64_t full[BATCH_STAGES], empty[BATCH_STAGES];
-  __shared__ StageInfo info[BATCH_STAGES];
+  __shared__ __align__(8) uint64_t full[BATCH_MAX_STAGES], empty[BATCH_MAX_STAGES];
+  __shared__ StageInfo info[BATCH_MAX_STAGES];
   const int tid = threadIdx.x, lane = tid & 31;
+  const unsigned S = (unsigned)stages;  // 2 .. BATCH_MAX_STAGES (checked by the host)
   if (tid == 0) {
-    for (int i = 0; i < BATCH_STAGES; ++i) {
+    for (unsigned i = 0; i < S; ++i) {
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], BATCH_CONSUMER_WARPS);
     }
@@ -294,13 +344,12 @@ __global__ void __launch_bounds__(BATCH_BLOCK, BREV_BATCHED_MIN_CTAS)
     // the current ticket runs out
     unsigned long long pending = 0;
     if (lane == 0) pending = atomicAdd(ticket_ctr, 1ull);
-    unsigned i = 0;
+    unsigned i = 0, st = 0, round = 0;  // st = i mod S, round = i div S
     bool ok = true;
 #pragma unroll 1
-    for (;; ++i) {
-      const int st = i % BATCH_STAGES;
-      if (i >= BATCH_STAGES) {  // wait until every consumer warp has read the stage
-        ok = mbar_wait_bounded(&empty[st], (i / BATCH_STAGES - 1) & 1);
+    for (;; ++i, st = st + 1 == S ? 0 : st + 1, round += st == 0) {
+      if (i >= S) {  // wait until every consumer warp has read the stage
+        ok = mbar_wait_bounded(&empty[st], (round - 1) & 1);
         if (!ok) break;
         fence_proxy_async_smem();
       }
@@ -319,8 +368,8 @@ __global__ void __launch_bounds__(BATCH_BLOCK, BREV_BATCHED_MIN_CTAS)
             a = 0;
             d = one;
           }
-          u = (unsigned)(t - d.first_ticket) * d.grain;
-          ulast = min(u + d.grain, d.units);
+          u = d.unit0 + (unsigned)(t - d.first_ticket) * d.grain;
+          ulast = min(u + d.grain, d.unit0 + d.units);
           if (lane == 0) pending = atomicAdd(ticket_ctr, 1ull);
         }
       }
@@ -338,19 +387,18 @@ __global__ void __launch_bounds__(BATCH_BLOCK, BREV_BATCHED_MIN_CTAS)
     // CTA may exit: units i-S+1 .. i-1, and unit i-S too after a timeout
     // (after the end marker, unit i-S's stage was released and its barrier
     // has moved on to the marker's phase)
-    const unsigned back = ok ? BATCH_STAGES - 1 : BATCH_STAGES;
+    const unsigned back = ok ? S - 1 : S;
     for (unsigned m = 1; m <= back && m <= i; ++m) {
       const unsigned j = i - m;
-      mbar_wait_bounded(&full[j % BATCH_STAGES], (j / BATCH_STAGES) & 1);
+      mbar_wait_bounded(&full[j % S], (j / S) & 1);
     }
     return;
   }
 
   // ---- consumer warps
 #pragma unroll 1
-  for (unsigned i = 0;; ++i) {
-    const int st = i % BATCH_STAGES;
-    if (!mbar_wait_bounded(&full[st], (i / BATCH_STAGES) & 1)) {
+  for (unsigned i = 0, st = 0, round = 0;; ++i, st = st + 1 == S ? 0 : st + 1, round += st == 0) {
+    if (!mbar_wait_bounded(&full[st], round & 1)) {
       if (lane == 0) atomicAdd(&g_batched_wait_timeouts, 1u);
       return;
     }
@@ -531,6 +579,8 @@ __device__ __forceinline__ int serve_next_ticket(const ServeArgs& A, BatchDesc& 
   d.E = __ldcg(&p->E);
   d.b = __ldcg(&p->b);
   d.mode = BATCH_BITREV;
+  d.unit0 = 0;
+  d.copy = batched_copy_default(d.E, d.b);
   seq = __ldcg(&p->seq);
   slot = sl;
   u = (unsigned)(t - d.first_ticket) * d.grain;
@@ -688,20 +738,107 @@ static int batched_b(int k, int E) {
   return batched_b_default(k, E);
 }
 
+// Staging of an array (k, E) at tile exponent b: the tuned one for the
+// array's usual tile exponent, else the built-in rule.
+static int batched_copy(int k, int E, int b) {
+  const int t = tuned_batched_copy(k, E);
+  if (b > 0 && t >= 0 && b == batched_b(k, E)) return t;
+  return batched_copy_default(E, b);
+}
+
+// Shared memory of one SM and the batched kernel's static shared memory,
+// read once per process (the library serves one GPU model at a time).
+static void batched_smem_limits(int* per_sm, int* per_block, int* static_bytes) {
+  static int sm = 0, blk = 0, st = 0;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    int dev = 0;
+    cudaFuncAttributes fa;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
+            cudaSuccess ||
+        cudaDeviceGetAttribute(&blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+            cudaSuccess ||
+        cudaFuncGetAttributes(&fa, (const void*)k_batched) != cudaSuccess) {
+      cudaGetLastError();
+      sm = 228 * 1024;
+      blk = 227 * 1024;
+      st = 1024;
+      return;
+    }
+    st = (int)fa.sharedSizeBytes;
+  });
+  *per_sm = sm;
+  *per_block = blk;
+  *static_bytes = st;
+}
+
+// Largest stage count whose shared memory fits one CTA (at least 2).
+static int batched_stages_cap(unsigned stage_bytes) {
+  int sm, blk, st;
+  batched_smem_limits(&sm, &blk, &st);
+  const int cap = stage_bytes ? (int)((unsigned)blk / stage_bytes) : BATCH_MAX_STAGES;
+  return std::max(2, std::min(BATCH_MAX_STAGES, cap));
+}
+
+// Built-in stage count: as many stages as fit while BREV_BATCHED_MIN_CTAS
+// CTAs share one SM's shared memory (each CTA also holds its static shared
+// memory and the 1 KiB the hardware reserves per CTA), 2 .. BATCH_MAX_STAGES.
+// More stages keep more bytes in flight per CTA: one 16 KiB tile pair of
+// 8-byte elements per CTA left the kernel latency-bound (5.2 TB/s on equal
+// arrays), two 32 KiB pairs do not.
+static int batched_stages_default(unsigned stage_bytes) {
+  int sm, blk, st;
+  batched_smem_limits(&sm, &blk, &st);
+  const int budget = sm / BREV_BATCHED_MIN_CTAS - 1024 - st;
+  const int s = stage_bytes ? budget / (int)stage_bytes : BATCH_MAX_STAGES;
+  return std::max(2, std::min(batched_stages_cap(stage_bytes), s));
+}
+
+int batched_stage_candidates(int k, int E, int b, int* out) {
+  if (!batched_b_valid(k, E, b)) return 0;
+  const int cap = batched_stages_cap(stage_unit_bytes(k, E, b));
+  int n = 0;
+  for (int s = 2; s <= cap; ++s) out[n++] = s;
+  return n;
+}
+
+static int batched_grid(unsigned smem) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched, BATCH_BLOCK, smem) !=
+          cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  return per_sm * current_device_sm_count();
+}
+
 struct BatchPlanData {
   std::vector<BatchDesc> desc;
   unsigned long long tickets = 0;
   unsigned stage_bytes = 0;  // shared memory of one pipeline stage
+  int stages = 0;            // pipeline stages per CTA
   std::vector<BatchItem> fallback;  // arrays run with single-array launches
 };
 
+// Tickets shrink once the work left is below BATCH_GUIDE tickets per CTA
+// (guided self-scheduling): a ticket of about 256 KiB keeps one CTA busy
+// for ~17 us on GB300, so a batch whose last tickets all had that size
+// ended on a tail of that length (14 us of a 1 GiB batch's 172 us).
+constexpr unsigned long long BATCH_GUIDE = 4;
+// Descriptors beyond one per array that the guided split may add.
+constexpr int BATCH_EXTRA_DESC = 24;
+
 // Descriptors and tickets of a batch; force_b >= 0 imposes that tile
-// exponent on every array (which must accept it).
+// exponent on every array (which must accept it), force_stages > 0 the
+// stage count.
 static brev_status build_batch(const BatchItem* items, int count, BatchPlanData* out,
-                               int force_b = -1) {
+                               int force_b = -1, int force_stages = 0, int force_copy = -1) {
   struct Tmp {
     BatchDesc d;
-    unsigned long long bytes;
+    unsigned long long bytes, unit_bytes;
+    unsigned stage;
   };
   std::vector<Tmp> tmp;
   tmp.reserve(count);
@@ -725,6 +862,7 @@ static brev_status build_batch(const BatchItem* items, int count, BatchPlanData*
     d.k = it.k;
     d.E = it.E;
     d.b = b;
+    d.copy = b == 0 ? BATCH_COPY_BULK : (force_copy >= 0 ? force_copy : batched_copy(it.k, it.E, b));
     unsigned long long unit_bytes;
     if (b == 0) {
       d.units = 1;
@@ -734,54 +872,90 @@ static brev_status build_batch(const BatchItem* items, int count, BatchPlanData*
       d.units = count_lt(w) + count_self(w);
       unit_bytes = 2ull * ((unsigned long long)it.E << (2 * b));
     }
-    out->stage_bytes = std::max(out->stage_bytes, stage_unit_bytes(it.k, it.E, b));
+    const unsigned stage = stage_unit_bytes(it.k, it.E, b);
+    // the array with the largest stage sets the stage count (tuned per
+    // (k, E), else as many as fit)
+    if (stage > out->stage_bytes) {
+      out->stage_bytes = stage;
+      const int ts = tuned_batched_stages(it.k, it.E);
+      out->stages = ts > 0 ? ts : 0;
+    }
     // about BATCH_TICKET_BYTES of tile data per ticket
     const unsigned long long g =
         std::max<unsigned long long>(1, BATCH_TICKET_BYTES / unit_bytes);
     d.grain = (unsigned)std::min<unsigned long long>(g, d.units);
-    tmp.push_back({d, (unsigned long long)it.E << it.k});
+    tmp.push_back({d, (unsigned long long)it.E << it.k, unit_bytes, stage});
   }
+  if (force_stages > 0) out->stages = force_stages;
+  if (out->stages <= 0) out->stages = batched_stages_default(out->stage_bytes);
+  out->stages = std::min(out->stages, batched_stages_cap(out->stage_bytes));
   // largest arrays first: the long-running tickets start early and the
   // small ones fill the tail
   std::stable_sort(tmp.begin(), tmp.end(),
                    [](const Tmp& a, const Tmp& b) { return a.bytes > b.bytes; });
+  // guided ticket sizes: while the work left W exceeds BATCH_GUIDE x CTAs
+  // x the ticket's bytes, keep the grain; below, halve it (down to one
+  // unit), splitting an array across descriptors where its grain changes
+  const unsigned long long P =
+      tmp.empty() ? 1 : (unsigned long long)batched_grid(out->stages * out->stage_bytes);
+  unsigned long long left = 0;
+  for (const auto& x : tmp) left += x.unit_bytes * x.d.units;
   unsigned long long t = 0;
-  out->desc.reserve(tmp.size());
+  int extra = 0;
+  out->desc.reserve(tmp.size() + BATCH_EXTRA_DESC);
   for (auto& x : tmp) {
-    x.d.first_ticket = t;
-    t += (x.d.units + x.d.grain - 1) / x.d.grain;
-    out->desc.push_back(x.d);
+    const unsigned long long ub = x.unit_bytes;
+    unsigned u = 0;
+    while (u < x.d.units) {
+      const unsigned long long want = left / (BATCH_GUIDE * P * ub);
+      unsigned long long g = x.d.grain;
+      while (g > 1 && g > want) g = (g + 1) / 2;
+      unsigned long long n = x.d.units - u;
+      if (g > 1 && extra < BATCH_EXTRA_DESC) {
+        // units at this grain until the work left falls below keep
+        const unsigned long long keep = g * BATCH_GUIDE * P * ub;
+        const unsigned long long m = (left - keep) / ub + 1;
+        n = std::min(n, (m + g - 1) / g * g);
+      } else if (g > 1) {
+        g = x.d.grain;  // no descriptor left for a split: finish the array as it is
+      }
+      BatchDesc d = x.d;
+      d.unit0 = u;
+      d.units = (unsigned)n;
+      d.grain = (unsigned)g;
+      d.first_ticket = t;
+      t += (n + g - 1) / g;
+      out->desc.push_back(d);
+      if (u > 0) ++extra;
+      u += (unsigned)n;
+      left -= n * ub;
+    }
   }
   out->tickets = t;
   return BREV_OK;
 }
 
-static int batched_grid(unsigned smem) {
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched, BATCH_BLOCK, smem) !=
-          cudaSuccess ||
-      per_sm < 1) {
-    cudaGetLastError();
-    per_sm = 1;
-  }
-  return per_sm * current_device_sm_count();
-}
-
 // Launch the persistent kernel over `count` descriptors already on the
-// device (ticket counter zeroed in stream order before it).
+// device (ticket counter zeroed in stream order before it), with `stages`
+// pipeline stages (0: the built-in count for the stage size).
 static brev_status launch_batched_kernel(const BatchDesc* d_desc, int count,
                                          unsigned long long tickets,
                                          unsigned long long* d_ticket, unsigned stage_bytes,
-                                         cudaStream_t stream, const BatchDesc* one = nullptr) {
+                                         int stages, cudaStream_t stream,
+                                         const BatchDesc* one = nullptr) {
   BatchDesc one_v{};
   if (one) one_v = *one;
-  const unsigned smem = BATCH_STAGES * stage_bytes;
+  if (stages <= 0) stages = batched_stages_default(stage_bytes);
+  if (stages < 2 || stages > BATCH_MAX_STAGES || stages > batched_stages_cap(stage_bytes))
+    return set_error(BREV_ERR_INVALID_ARG, "stage count %d for stages of %u bytes", stages,
+                     stage_bytes);
+  const unsigned smem = (unsigned)stages * stage_bytes;
   cudaError_t e = ensure_smem((const void*)k_batched, smem);
   if (e != cudaSuccess) return cuda_error(e, "shared-memory limit of the batched kernel");
   const int grid =
       (int)std::min<unsigned long long>((unsigned long long)batched_grid(smem), tickets);
   void* args[] = {(void*)&d_desc, (void*)&count, (void*)&one_v, (void*)&tickets,
-                  (void*)&d_ticket, (void*)&stage_bytes};
+                  (void*)&d_ticket, (void*)&stage_bytes, (void*)&stages};
   e = cudaLaunchKernel((const void*)k_batched, dim3(grid), dim3(BATCH_BLOCK), args, smem,
                        stream);
   if (e != cudaSuccess) return cuda_error(e, "batched kernel launch");
@@ -797,7 +971,7 @@ static brev_status enqueue_batch(const BatchPlanData& p, const BatchDesc* d_desc
     cudaError_t e = cudaMemsetAsync(d_ticket, 0, sizeof(unsigned long long), stream);
     if (e != cudaSuccess) return cuda_error(e, "ticket reset");
     brev_status s = launch_batched_kernel(d_desc, (int)p.desc.size(), p.tickets, d_ticket,
-                                          p.stage_bytes, stream);
+                                          p.stage_bytes, p.stages, stream);
     if (s != BREV_OK) return s;
   }
   for (const BatchItem& it : p.fallback) {
@@ -813,13 +987,13 @@ void preload_batched() {
 }
 
 brev_status batched_launch(const BatchItem* items, int count, cudaStream_t stream) {
-  return batched_launch_forced(items, count, -1, stream);
+  return batched_launch_forced(items, count, -1, 0, -1, stream);
 }
 
-brev_status batched_launch_forced(const BatchItem* items, int count, int b,
+brev_status batched_launch_forced(const BatchItem* items, int count, int b, int stages, int copy,
                                   cudaStream_t stream) {
   BatchPlanData p;
-  brev_status s = build_batch(items, count, &p, b);
+  brev_status s = build_batch(items, count, &p, b, stages, copy);
   if (s != BREV_OK) return s;
   if (p.desc.empty()) return enqueue_batch(p, nullptr, nullptr, stream);
   // stream-ordered workspace: descriptors + ticket counter
@@ -865,13 +1039,15 @@ brev_status bitrev_inplace_pipelined(void* data, int k, int E, int b, cudaStream
   d.E = E;
   d.b = b;
   d.mode = BATCH_BITREV;
+  d.copy = batched_copy_default(E, b);
   const int w = k - 2 * b;
   const unsigned long long units = (unsigned long long)count_lt(w) + count_self(w);
   if (units > 0xFFFFFFFFull) return set_error(BREV_ERR_UNSUPPORTED, "too many tile units");
   d.units = (unsigned)units;
   // about 8 tickets per resident CTA (the tail of the last wave stays short)
   const unsigned stage = stage_unit_bytes(k, E, b);
-  const unsigned long long ctas = (unsigned long long)batched_grid(BATCH_STAGES * stage);
+  const int stages = batched_stages_default(stage);
+  const unsigned long long ctas = (unsigned long long)batched_grid(stages * stage);
   const unsigned long long unit_bytes = 2ull * ((unsigned long long)E << (2 * b));
   d.grain = (unsigned)std::min<unsigned long long>(
       std::max<unsigned long long>(1, units / (8 * ctas)),
@@ -890,13 +1066,15 @@ brev_status bitrev_inplace_pipelined(void* data, int k, int E, int b, cudaStream
     ws_free(ws, stream);
     return cuda_error(e, "ticket reset");
   }
-  brev_status st = launch_batched_kernel(nullptr, 0, tickets, d_ticket, stage, stream, &d);
+  brev_status st =
+      launch_batched_kernel(nullptr, 0, tickets, d_ticket, stage, stages, stream, &d);
   ws_free(ws, stream);
   return st;
 }
 
 size_t batched_ws_bytes(int count) {
-  return ((size_t)std::max(count, 0) * sizeof(BatchDesc) + 15) / 16 * 16 + 64;
+  return ((size_t)(std::max(count, 0) + BATCH_EXTRA_DESC) * sizeof(BatchDesc) + 15) / 16 * 16 +
+         64;
 }
 
 brev_status batched_launch_into(const BatchItem* items, int count, void* ws, size_t ws_bytes,
@@ -906,7 +1084,7 @@ brev_status batched_launch_into(const BatchItem* items, int count, void* ws, siz
   if (s != BREV_OK) return s;
   if (p.desc.empty()) return enqueue_batch(p, nullptr, nullptr, stream);
   const size_t desc_bytes = p.desc.size() * sizeof(BatchDesc);
-  if (!ws || batched_ws_bytes((int)p.desc.size()) > ws_bytes)
+  if (!ws || ((desc_bytes + 15) / 16) * 16 + 64 > ws_bytes)
     return set_error(BREV_ERR_INVALID_ARG, "batched workspace too small");
   // pageable source: staged before the call returns
   cudaError_t e = cudaMemcpyAsync(ws, p.desc.data(), desc_bytes, cudaMemcpyHostToDevice, stream);
@@ -934,6 +1112,7 @@ brev_status transpose_inplace_pipelined(void* data, int a, int E, cudaStream_t s
   d.E = E;
   d.b = b;
   d.mode = BATCH_TRANSPOSE;
+  d.copy = batched_copy_default(E, b);
   const unsigned long long T = 1ull << (a - b);
   const unsigned long long units = T * (T - 1) / 2 + T;
   if (units > 0xFFFFFFFFull)
@@ -959,7 +1138,7 @@ brev_status transpose_inplace_pipelined(void* data, int a, int E, cudaStream_t s
     return cuda_error(e, "ticket reset");
   }
   brev_status st = launch_batched_kernel(nullptr, 0, tickets, d_ticket,
-                                         stage_unit_bytes(2 * b, E, b), stream, &d);
+                                         stage_unit_bytes(2 * b, E, b), 0, stream, &d);
   ws_free(ws, stream);
   return st;
 }
@@ -1250,8 +1429,8 @@ static brev_status noalloc_scratch(void** out) {
   return BREV_OK;
 }
 
-// Host-side staging in one fixed static block (guarded by g_noalloc_mu for
-// the whole call): nothing is allocated on the host either.
+// Host-side staging in one fixed static block (guarded by g_noalloc_call_mu
+// for the whole call): nothing is allocated on the host either.
 struct NoallocHost {
   BatchDesc desc[NOALLOC_MAX_ARRAYS];
   BatchItem fallback[NOALLOC_MAX_ARRAYS];
@@ -1323,6 +1502,7 @@ extern "C" brev_status brev_permute_batched_noalloc(void* const* ptr_array,
     d.k = it.k;
     d.E = it.E;
     d.b = b;
+    d.copy = b == 0 ? BATCH_COPY_BULK : batched_copy(it.k, it.E, b);
     unsigned long long unit_bytes;
     if (b == 0) {
       d.units = 1;
@@ -1364,7 +1544,7 @@ extern "C" brev_status brev_permute_batched_noalloc(void* const* ptr_array,
     if (e != cudaSuccess) return cuda_error(e, "descriptor upload (no-alloc)");
     e = cudaMemsetAsync(d_ticket, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return cuda_error(e, "ticket reset (no-alloc)");
-    s = launch_batched_kernel(d_desc, nd, tickets, d_ticket, stage_bytes, st);
+    s = launch_batched_kernel(d_desc, nd, tickets, d_ticket, stage_bytes, 0, st);
     if (s != BREV_OK) return s;
   }
   for (int i = 0; i < nf; ++i) {

@@ -75,10 +75,16 @@ brev_status batched_launch(const BatchItem* items, int count, cudaStream_t strea
 size_t batched_ws_bytes(int count);
 brev_status batched_launch_into(const BatchItem* items, int count, void* ws, size_t ws_bytes,
                                 cudaStream_t stream);
-// The same launch with tile exponent `b` forced for every array (the
-// tuner's candidates; each array must accept b, see batched_candidates).
-brev_status batched_launch_forced(const BatchItem* items, int count, int b,
+// The same launch with tile exponent `b` forced for every array (b < 0:
+// the usual choice; each array must accept b, see batched_candidates) and
+// `stages` pipeline stages (0: the usual choice) and tile rows staged as
+// `copy` (0: bulk copies, 1: per-thread chunks, -1: the usual choice) --
+// the tuner's candidates.
+brev_status batched_launch_forced(const BatchItem* items, int count, int b, int stages, int copy,
                                   cudaStream_t stream);
+// Stage counts the batched kernel can run with stages of the array (k, E)
+// at tile exponent b, into out[0..return).
+int batched_stage_candidates(int k, int E, int b, int* out);
 // Tile exponents the batched kernel can use for an array (k, E), into
 // out[0..return); the built-in choice in *def.  0 candidates: the array is
 // not run by the batched kernel.
@@ -133,8 +139,12 @@ bool resident_shape(int k, int E, int ctas, int* b, unsigned* units, unsigned* g
 bool pipeline_shape_ok(int k, int E, int b);
 int pipeline_shapes(int E, int* out);
 brev_status bitrev_inplace_pipelined(void* data, int k, int E, int b, cudaStream_t stream);
-// Tuned batched tile exponent for (k, E), or -1 (brev_api.cu).
+// Tuned batched tile exponent for (k, E), or -1, and tuned stage count of
+// a batch whose largest stage is this array's, or 0 (brev_api.cu).
 int tuned_batched_b(int k, int E);
+int tuned_batched_stages(int k, int E);
+// Tuned staging of the array's tile rows (0 bulk, 1 chunks), or -1.
+int tuned_batched_copy(int k, int E);
 // Argument checks of a batch (sizes, alignment, device ranges, no overlap).
 brev_status validate_batch_items(const BatchItem* items, int count);
 // Launch one permutation without argument checks (src == dst: in-place).

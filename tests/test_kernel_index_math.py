@@ -280,10 +280,12 @@ def batched_stage_bytes(k, E, b):
     return (raw + 127) & ~127
 
 
-def emulate_staged_unit(E, b, k, u, nthr=256, transpose=False):
-    """Replay one unit of the TMA-staged batched kernel: the bulk copies
-    the producer warp issues (row x of each tile to padded row rev(x), or x
-    for a transposition) and the store phase of the consumer threads.
+def emulate_staged_unit(E, b, k, u, nthr=256, transpose=False, copy=0):
+    """Replay one unit of the TMA-staged batched kernel: the copies the
+    producer warp issues (row x of each tile to padded row rev(x), or x for
+    a transposition; copy 0: one bulk copy per row, copy 1: the rows'
+    16-byte chunks spread over the 32 lanes) and the store phase of the
+    consumer threads.
     Bit reversal: an array of 2^k elements; transposition: a 2^k x 2^k
     matrix.  Returns (copied source elements, stores as (destination
     element, source element), read-slot conflicts)."""
@@ -329,18 +331,38 @@ def emulate_staged_unit(E, b, k, u, nthr=256, transpose=False):
         a_off, r_off = (y << b) * E, (ry << b) * E
         rmap = lambda x: brev(x, b)
     tx = 0
-    for q in range(nt * rows):
-        t, x = q >> b, q & (rows - 1)
-        dst = t * rows * pitch + rmap(x) * pitch
-        src = (r_off if t else a_off) + x * stride
-        assert dst % 16 == 0 and src % 16 == 0 and rowb % 16 == 0
-        assert 0 <= dst and dst + rowb <= stage and 0 <= src and src + rowb <= n * E
-        for o in range(0, rowb, E):
-            assert dst + o not in smem
-            smem[dst + o] = (src + o) // E
-            loads.append((src + o) // E)
-        tx += rowb
-    assert tx == nt * rows * rowb  # the byte count lane 0 expects
+    if copy == 0:
+        for q in range(nt * rows):
+            t, x = q >> b, q & (rows - 1)
+            dst = t * rows * pitch + rmap(x) * pitch
+            src = (r_off if t else a_off) + x * stride
+            assert dst % 16 == 0 and src % 16 == 0 and rowb % 16 == 0
+            assert 0 <= dst and dst + rowb <= stage and 0 <= src and src + rowb <= n * E
+            for o in range(0, rowb, E):
+                assert dst + o not in smem
+                smem[dst + o] = (src + o) // E
+                loads.append((src + o) // E)
+            tx += rowb
+        assert tx == nt * rows * rowb  # the byte count lane 0 expects
+    else:
+        cpr = rowb // 16
+        log_cpr = cpr.bit_length() - 1
+        assert cpr == 1 << log_cpr
+        chunks = nt * (rows << log_cpr)
+        assert chunks % 32 == 0  # every lane issues the same number of copies
+        for lane in range(32):
+            for q in range(lane, chunks, 32):
+                c = q & (cpr - 1)
+                tx_ = q >> log_cpr
+                t, x = tx_ >> b, tx_ & (rows - 1)
+                dst = t * rows * pitch + rmap(x) * pitch + c * 16
+                src = (r_off if t else a_off) + x * stride + c * 16
+                assert dst % 16 == 0 and src % 16 == 0
+                assert 0 <= dst and dst + 16 <= stage and 0 <= src and src + 16 <= n * E
+                for o in range(0, 16, E):
+                    assert dst + o not in smem
+                    smem[dst + o] = (src + o) // E
+                    loads.append((src + o) // E)
     V = 16 // E
     log_v = V.bit_length() - 1
     log_c = b - log_v
@@ -374,11 +396,13 @@ BATCHED_SHAPES = {16: (3, 4, 5), 8: (4, 5), 4: (5, 6)}
 BATCHED_BMIN = {16: 3, 8: 4, 4: 5}
 
 
+@pytest.mark.parametrize("copy", (0, 1))
 @pytest.mark.parametrize("E", sorted(BATCHED_SHAPES))
-def test_batched_staged_index_math(E):
-    """TMA-staged batched kernel: copies in bounds, 16-byte aligned and
-    counted in the expected bytes; every staged chunk read once per tile
-    without bank conflicts; every element moved once to rev(i)."""
+def test_batched_staged_index_math(E, copy):
+    """TMA-staged batched kernel, tile rows staged as bulk copies (copy 0)
+    or as per-thread 16-byte chunks (copy 1): copies in bounds, 16-byte
+    aligned and counted in the expected bytes; every staged chunk read once
+    per tile without bank conflicts; every element moved once to rev(i)."""
     cases = [(k, 0) for k in range(2, 16)
              if k < 2 * BATCHED_BMIN[E] or (E << k) <= 32768]   # whole array staged
     cases += [(k, b) for b in BATCHED_SHAPES[E] for k in range(2 * b, 2 * b + 4)
@@ -387,7 +411,7 @@ def test_batched_staged_index_math(E):
         units = 1 if b == 0 else count_lt(k - 2 * b) + count_self(k - 2 * b)
         loads, stores, conf = [], [], 0
         for u in range(units):
-            lo, st, c = emulate_staged_unit(E, b, k, u)
+            lo, st, c = emulate_staged_unit(E, b, k, u, copy=copy)
             loads += lo
             stores += st
             conf += c
@@ -399,7 +423,7 @@ def test_batched_staged_index_math(E):
         T = 1 << (a - b)
         loads, stores, conf = [], [], 0
         for u in range(T * (T - 1) // 2 + T):
-            lo, st, c = emulate_staged_unit(E, b, a, u, transpose=True)
+            lo, st, c = emulate_staged_unit(E, b, a, u, transpose=True, copy=copy)
             loads += lo
             stores += st
             conf += c
@@ -449,6 +473,71 @@ def test_batched_array_search():
         for t in list(range(0, min(total, 300))) + rng.integers(0, total, 300).tolist():
             a = find_array(first, int(t))
             assert first[a] <= t < (first[a + 1] if a + 1 < count else total)
+
+
+def guided_schedule(arrays, ctas, guide=4, ticket_bytes=262144, extra_max=24):
+    """Host-side ticket schedule of the batched launch, restated: arrays
+    (units, unit_bytes), largest first; the grain (units per ticket) is
+    about ticket_bytes of tiles and is halved, down to one unit, whenever the
+    work left falls below guide x ctas x the ticket's bytes, splitting an
+    array across descriptors (unit0, units, grain, first_ticket)."""
+    order = sorted(range(len(arrays)), key=lambda i: -arrays[i][0] * arrays[i][1])
+    left = sum(u * ub for u, ub in arrays)
+    t, extra, desc = 0, 0, []
+    for a in order:
+        units, ub = arrays[a]
+        gmax = min(max(1, ticket_bytes // ub), units)
+        u = 0
+        while u < units:
+            want = left // (guide * ctas * ub)
+            g = gmax
+            while g > 1 and g > want:
+                g = (g + 1) // 2
+            n = units - u
+            if g > 1 and extra < extra_max:
+                keep = g * guide * ctas * ub
+                m = (left - keep) // ub + 1
+                n = min(n, (m + g - 1) // g * g)
+            elif g > 1:
+                g = gmax
+            desc.append((a, u, n, g, t, left, extra < extra_max))
+            t += -(-n // g)
+            if u > 0:
+                extra += 1
+            u += n
+            left -= n * ub
+    return desc, t
+
+
+def test_batched_guided_schedule():
+    """Every unit of every array in exactly one ticket; descriptors in
+    ticket order; while descriptors are left for splits, no ticket holds
+    more than the work left at its start / (guide x CTAs), or one unit;
+    at most 24 descriptors beyond one per array."""
+    rng = np.random.default_rng(11)
+    cases = [[(count_lt(w) + count_self(w), 32768)] * c for w, c in ((14, 2), (12, 8), (10, 64))]
+    cases += [[(int(rng.integers(1, 2000)), int(rng.choice([2048, 8192, 16384, 32768])))
+               for _ in range(int(rng.integers(1, 200)))] for _ in range(15)]
+    for arrays in cases:
+        for ctas in (1, 152, 456):
+            desc, tickets = guided_schedule(arrays, ctas)
+            covered = {}
+            seen_t = 0
+            for a, u0, n, g, ft, left, split_ok in desc:
+                if split_ok:
+                    assert g == 1 or g * arrays[a][1] * 4 * ctas <= left
+                assert ft == seen_t and n >= 1 and g >= 1
+                seen_t += -(-n // g)
+                for tk in range(-(-n // g)):
+                    lo, hi = u0 + tk * g, min(u0 + (tk + 1) * g, u0 + n)
+                    for u in range(lo, hi):
+                        assert (a, u) not in covered
+                        covered[(a, u)] = ft + tk
+            assert seen_t == tickets
+            assert len(covered) == sum(u for u, _ in arrays)
+            assert len(desc) <= len(arrays) + 24
+            if desc[-1][6]:
+                assert desc[-1][3] == 1  # the last tickets are single units
 
 
 @pytest.mark.parametrize("E", (16, 8, 4))
@@ -921,15 +1010,28 @@ class _MBar:
         self.tx -= n
         self._check()
 
+    def async_arrive_register(self):
+        """cp.async.mbarrier.arrive (no .noinc): pending rises now and
+        falls when the thread's copies land (async_arrive_done)."""
+        self.pending += 1
+
+    def async_arrive_done(self):
+        self.pending -= 1
+        assert self.pending >= 0
+        self._check()
+
     def try_wait(self, parity):
         return (self.completed & 1) != parity
 
 
-def simulate_batched_pipeline(n_units, S, n_consumers, seed):
+def simulate_batched_pipeline(n_units, S, n_consumers, seed, lanes=0):
     """Random interleavings of the batched kernel's producer warp, its
     consumer warps and the copy engine, following the kernel's waits and
     arrivals; fails on a read before the bytes land, a stage overwritten
-    while read, a lost or repeated unit, or a wait that can never end."""
+    while read, a lost or repeated unit, or a wait that can never end.
+    lanes = 0: bulk copies (lane 0's arrival carries the byte count);
+    lanes > 0: that many lanes' per-thread copies, each lane tied to the
+    barrier by an asynchronous arrival, then lane 0's plain arrival."""
     rng = np.random.default_rng(seed)
     full = [_MBar(1) for _ in range(S)]
     empty = [_MBar(n_consumers) for _ in range(S)]
@@ -950,10 +1052,18 @@ def simulate_batched_pipeline(n_units, S, n_consumers, seed):
                 info[st] = -1
                 full[st].arrive()
                 break
-            info[st] = i
             owner[st] = i
-            full[st].arrive(expect_tx=64)
-            inflight.append((st, i))
+            if lanes == 0:
+                info[st] = i
+                full[st].arrive(expect_tx=64)
+                inflight.append((st, i, None))
+            else:
+                for lane in range(lanes):  # copies issued, then the async arrivals
+                    full[st].async_arrive_register()
+                    inflight.append((st, i, lane))
+                yield lambda: True  # __syncwarp: the lanes' copies may land meanwhile
+                info[st] = i
+                full[st].arrive()
             i += 1
         for m in range(1, S):
             if m > i:
@@ -989,9 +1099,14 @@ def simulate_batched_pipeline(n_units, S, n_consumers, seed):
         assert choices, "deadlock: no actor can proceed"
         c = choices[rng.integers(len(choices))]
         if c == "copy":
-            st, u = inflight.pop(rng.integers(len(inflight)))
-            landed.add(u)
-            full[st].complete_tx(64)
+            st, u, lane = inflight.pop(rng.integers(len(inflight)))
+            if lane is None:
+                landed.add(u)
+                full[st].complete_tx(64)
+            else:
+                if not any(x[1] == u for x in inflight):
+                    landed.add(u)  # the unit's last lane landed
+                full[st].async_arrive_done()
         else:
             nxt = next(actors[c], None)
             if nxt is None:
@@ -1004,8 +1119,9 @@ def simulate_batched_pipeline(n_units, S, n_consumers, seed):
         assert consumed[w] == list(range(n_units))
 
 
-@pytest.mark.parametrize("S", [2, 3, 4])
-def test_batched_pipeline_protocol(S):
+@pytest.mark.parametrize("lanes", [0, 3])
+@pytest.mark.parametrize("S", [2, 3, 4, 5, 6])
+def test_batched_pipeline_protocol(S, lanes):
     for n_units in (0, 1, 2, S, S + 1, 7, 23):
         for seed in range(12):
-            simulate_batched_pipeline(n_units, S, 8, seed * 31 + n_units)
+            simulate_batched_pipeline(n_units, S, 8, seed * 31 + n_units, lanes)
