@@ -35,6 +35,9 @@ sys.path.insert(0, ROOT)
 SWEEP_KS = list(range(10, 29))
 SWEEP_KINDS = [("u32", 4), ("f32", 4), ("c64", 8), ("c128", 16)]
 FALLBACK_PEAK_GBS = 6800.0
+# what the timed path moves: whole elements of the sweep's kinds, as opaque
+# bytes (nothing is computed or narrowed)
+DTYPE_LABEL = "opaque 4/8/16-byte elements (exact)"
 # FP64 FMA thread-instructions per SM per cycle on GB300 (ncu's issue peak,
 # sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained = 304 over
 # 152 SMs)
@@ -64,6 +67,10 @@ def parse_args():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-next", action="store_true")
     ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--no-midsize", action="store_true")
+    ap.add_argument("--no-serve-sweep", action="store_true")
+    ap.add_argument("--sweep-seconds", type=float, default=2.0,
+                    help="seconds of arrivals per point of the serving rate sweep")
     ap.add_argument("--points-out", default=None,
                     help="write per-point median times of the sweep to this JSON file")
     ap.add_argument("--next-k", type=int, default=28,
@@ -386,6 +393,13 @@ def run_brev(args):
             torch, brev, inputs, device, stream, sampler, reduce_max, barrier, peak,
             info["nominal_gbs"]))
 
+    # ----------------------- mid-size arrays, back to back (cfg 2 detail)
+    midsize = None
+    if not args.no_midsize:
+        midsize = section("midsize", lambda: bench_midsize(
+            torch, brev, device, stream, sampler, reduce_max, barrier, peak,
+            info["l2_bytes"]))
+
     # -------------------------------------------- widened rows (NEXT)
     next_rows = None
     if not args.no_next:
@@ -408,10 +422,14 @@ def run_brev(args):
         torch.cuda.empty_cache()
         sampler.pause()
         arena = torch.empty(16 << 30, dtype=torch.uint8, device=device)
-        native = section("serving", lambda: brev.brev_server_run_poisson(
-            arena, seed=5, rate_per_s=20000.0, seconds=args.serve_seconds)[0])
-        resident = section("resident serving", lambda: brev.brev_server_run_poisson(
-            arena, seed=5, rate_per_s=20000.0, seconds=args.serve_seconds, resident=True)[0])
+        native = section("serving", lambda: traced_run(brev, arena, resident=False,
+                                                       seconds=args.serve_seconds))
+        resident = section("resident serving", lambda: traced_run(
+            brev, arena, resident=True, seconds=args.serve_seconds))
+        rate_sweep = None
+        if not args.no_serve_sweep:
+            rate_sweep = section("serving rate sweep", lambda: serving_rate_sweep(
+                brev, arena, args.sweep_seconds))
         del arena
         torch.cuda.empty_cache()
         py = section("python serving", lambda: serve_poisson(
@@ -431,7 +449,9 @@ def run_brev(args):
                     "per request)",
             **{k: (round(v, 1) if isinstance(v, float) else v) for k, v in resident.items()
                if k in ("completed", "p50_us", "p99_us", "max_us", "mean_us", "queue_p99_us",
-                        "gbs", "launches", "max_inflight", "peak_pool_bytes", "error")}}
+                        "gbs", "launches", "max_inflight", "peak_pool_bytes", "error",
+                        "by_size")}}
+        serving["rate_sweep"] = rate_sweep
         serving["python_loop"] = {k: py[k] for k in ("completed", "p50_us", "p99_us", "gbs",
                                                      "mean_batch", "error") if k in py}
     sampler.stop()
@@ -449,7 +469,7 @@ def run_brev(args):
             "value": round(value, 1), "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "u8",
+            "dtype": DTYPE_LABEL,
             "data": "synthetic (seeded SplitMix64: uint32, float32 U[-1,1), complex<float>, "
                     "complex<double>)",
             "config": sweep_config(args.kmax, args.kinds, ws, info["l2_bytes"] >> 20),
@@ -461,6 +481,7 @@ def run_brev(args):
             "batched": batched,
             "serving": serving,
             "large_single_arrays": large_cfg,
+            "midsize_back_to_back": midsize,
             "transpositions_and_recursive": next_rows,
             "e2e": e2e,
             "gpu_launches": int(launches),
@@ -549,6 +570,122 @@ def bench_large(torch, brev, inputs, device, stream, sampler, reduce_max, barrie
     return out
 
 
+def _graph_of(torch, stream, fns):
+    """A CUDA graph of the launches fns() enqueue on `stream`."""
+    g = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=stream, capture_error_mode="thread_local"):
+        for f in fns:
+            f()
+    return g
+
+
+def _replay_ms(torch, stream, g, reps=3):
+    """Mean time of one replay of graph g (two warm-up replays first)."""
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        g.replay()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def bench_midsize(torch, brev, device, stream, sampler, reduce_max, barrier, peak, l2_bytes,
+                  ks=range(18, 26), kinds=(("f32", 4), ("c64", 8), ("c128", 16))):
+    """Single arrays of k = 18..25 timed as R back-to-back launches captured
+    in one CUDA graph (no event between launches).  cold: the launches
+    rotate over buffer sets whose footprint together exceeds 3x L2, so every
+    launch reads its input from HBM; warm: one buffer set (out of place
+    ping-pong), L2-resident when it fits; copy: torch's device copy of the
+    same bytes, timed the same way -- the per-launch ceiling any kernel of
+    that size meets.  Beside them, C equal arrays of about 1 GiB in all: the
+    loop of C single launches (one graph) against one batched launch (a
+    plan)."""
+    L = brev.lib()
+    sh = stream.cuda_stream
+    out = {"method": "R launches per CUDA graph replay; GB/s = 2 n E x R / replay time; "
+                     "cold rotates buffers totalling > 3x L2, warm reuses one set",
+           "points": {}, "batched_vs_loop": {}}
+    w0 = time.time()
+    for kind, E in kinds:
+        for k in ks:
+            nb = E << k
+            for ip in (False, True):
+                foot = nb if ip else 2 * nb
+                M = max(1, min(-(-3 * l2_bytes // foot), (6 << 30) // foot))
+                bufs = [torch.empty(nb, dtype=torch.uint8, device=device)
+                        for _ in range(M if ip else 2 * M)]
+                for b_ in bufs:
+                    b_.fill_(0x5A)
+                sets = ([(b_, b_) for b_ in bufs] if ip else
+                        [(bufs[2 * i + 1], bufs[2 * i]) for i in range(M)])
+                R = max(8, min(256, int(4e-3 / (2 * nb / 6.5e12))))
+
+                def launch(d, s_):
+                    return lambda: L.brev_permute_to(d.data_ptr(), s_.data_ptr(), k, E, sh)
+                cold = [launch(*sets[r % M]) for r in range(R)]
+                d0, s0 = sets[0]
+                warm = [launch(d0, s0) if (ip or r % 2 == 0) else launch(s0, d0)
+                        for r in range(R)]
+                rec = {}
+                for name, fns in (("cold", cold), ("warm", warm)):
+                    g = _graph_of(torch, stream, fns)
+                    ms = _replay_ms(torch, stream, g) / R
+                    rec[f"{name}_gbs"] = round(2 * nb / (ms * 1e-3) / 1e9, 1)
+                    del g
+                if not ip:
+                    f32 = [(d.view(torch.float32), s_.view(torch.float32)) for d, s_ in sets]
+                    g = _graph_of(torch, stream,
+                                  [lambda d=f32[r % M][0], s_=f32[r % M][1]: d.copy_(s_)
+                                   for r in range(R)])
+                    ms = _replay_ms(torch, stream, g) / R
+                    rec["copy_cold_gbs"] = round(2 * nb / (ms * 1e-3) / 1e9, 1)
+                    del g
+                rec["cold_frac"] = round(rec["cold_gbs"] / peak, 4)
+                rec["tile"] = list(brev.brev_tile_shape(k, E, ip))
+                out["points"][f"{kind}_{'ip' if ip else 'oop'}_k{k}"] = rec
+                del bufs, sets, cold, warm
+                torch.cuda.empty_cache()
+        for k in range(18, 25):
+            nb = E << k
+            C = max(2, min(512, (1 << 30) // nb))
+            arrs = [torch.full((nb,), 3, dtype=torch.uint8, device=device) for _ in range(C)]
+            views = [a.view({4: torch.float32, 8: torch.complex64, 16: torch.complex128}[E])
+                     for a in arrs]
+            g = _graph_of(torch, stream,
+                          [lambda a=a: L.brev_permute_to(a.data_ptr(), a.data_ptr(), k, E, sh)
+                           for a in arrs])
+            loop_ms = _replay_ms(torch, stream, g)
+            del g
+            plan = brev.BrevPlan(views)
+            for _ in range(2):
+                plan.launch(stream)
+            torch.cuda.synchronize()
+            ea = torch.cuda.Event(enable_timing=True)
+            eb = torch.cuda.Event(enable_timing=True)
+            ea.record(stream)
+            for _ in range(8):
+                plan.launch(stream)
+            eb.record(stream)
+            torch.cuda.synchronize()
+            plan_ms = ea.elapsed_time(eb) / 8
+            plan.close()
+            tot = 2 * nb * C
+            out["batched_vs_loop"][f"{kind}_k{k}_x{C}"] = {
+                "loop_gbs": round(tot / (loop_ms * 1e-3) / 1e9, 1),
+                "batched_gbs": round(tot / (plan_ms * 1e-3) / 1e9, 1),
+                "speedup": round(loop_ms / plan_ms, 3)}
+            del arrs, views
+            torch.cuda.empty_cache()
+    sampler.window(w0, time.time())
+    return out
+
+
 def bench_next(torch, brev, inputs, device, stream, sampler, reduce_max, barrier, peak,
                reps=5, warm=2, k=28):
     """The widened rows: transpositions (square and narrow: the even-odd step
@@ -582,12 +719,17 @@ def bench_next(torch, brev, inputs, device, stream, sampler, reduce_max, barrier
         "one_pass_gbs": round(nbytes / (one * 1e-3) / 1e9, 1),
         "recursive_hbm_passes": 3}
     # bit reversal fused with the first DIT FFT stages vs the plain permutation.
-    # complex<double> stages are bound by the FP64 pipe: its peak is the SM
-    # count x 2 FP64 FMA per SM per cycle (the issue peak ncu reports for
-    # GB300) x 2 flops x the maximum SM clock nvidia-smi reports.
+    # complex<double> stages are bound by the FP64 pipe: the peak is measured
+    # on this GPU in the same run (brev_fp64_fma_tflops: independent FMA
+    # chains on every SM); beside it the figure derived from the SM count,
+    # 2 FP64 FMA per SM per cycle (the issue peak ncu reports for GB300),
+    # 2 flops and the maximum SM clock nvidia-smi reports.
     sm_count = torch.cuda.get_device_properties(device).multi_processor_count
     max_mhz = max((smp[2] for smp in sampler.samples), default=None)
-    fp64_peak = sm_count * FP64_FMA_PER_SM_CLK * 2 * max_mhz * 1e6 / 1e12 if max_mhz else None
+    fp64_derived = sm_count * FP64_FMA_PER_SM_CLK * 2 * max_mhz * 1e6 / 1e12 if max_mhz else None
+    w0 = time.time()
+    fp64_peak = brev.brev_fp64_fma_tflops()
+    sampler.window(w0, time.time())
     for kind, E, S in (("c64", 8, 6), ("c128", 16, 5)):
         k2 = k
         x = torch.empty((1 << k2) * E, dtype=torch.uint8, device=device)
@@ -611,10 +753,77 @@ def bench_next(torch, brev, inputs, device, stream, sampler, reduce_max, barrier
                 "bound": "alu", "unit": "TFLOP/s", "achieved": round(ach, 3),
                 "peak": round(fp64_peak, 3), "frac": round(ach / fp64_peak, 4),
                 "counted": "5 n flops per radix-2 stage",
-                "peak_source": f"{sm_count} SMs x {FP64_FMA_PER_SM_CLK} FP64 FMA/SM/cycle x 2 flops "
-                               f"x {max_mhz:.0f} MHz (derived)"}
+                "peak_source": "measured in this run: FP64 FMA chains on every SM "
+                               "(brev_fp64_fma_tflops), 2 flops per FMA",
+                "derived_peak": round(fp64_derived, 3) if fp64_derived else None,
+                "derived_from": (f"{sm_count} SMs x {FP64_FMA_PER_SM_CLK} FP64 FMA/SM/cycle x "
+                                 f"2 flops x {max_mhz:.0f} MHz") if max_mhz else None}
         del x, y
     del src, dst
+    return out
+
+
+SIZE_CLASSES = ((10, 16), (17, 20), (21, 22), (23, 24))
+
+
+def latency_by_size(trace):
+    """Per-request latency (completion seen by the serving thread -
+    arrival, from the trace) by array size class: count, p50, p99 and the
+    share of the run's slowest 1 % that the class holds."""
+    import numpy as np
+    trace = [r for r in (trace or []) if r["seen_us"] > 0]
+    if not trace:
+        return None
+    lat = np.array([r["seen_us"] - r["arrival_us"] for r in trace])
+    ks = np.array([r["log2n"] for r in trace])
+    cut = np.percentile(lat, 99)
+    slow = lat >= cut
+    out = {}
+    for lo, hi in SIZE_CLASSES:
+        m = (ks >= lo) & (ks <= hi)
+        if not m.any():
+            continue
+        out[f"k{lo}-{hi}"] = {"count": int(m.sum()),
+                              "p50_us": round(float(np.percentile(lat[m], 50)), 1),
+                              "p99_us": round(float(np.percentile(lat[m], 99)), 1),
+                              "share_of_slowest_1pct": round(float((slow & m).sum() / slow.sum()), 3)}
+    return out
+
+
+def traced_run(brev, arena, resident, seconds, rate=20000.0):
+    """The 20k req/s headline run of one serving mode, with the per-request
+    trace summarised by size class."""
+    st, tr = brev.brev_server_run_poisson(arena, seed=5, rate_per_s=rate, seconds=seconds,
+                                          resident=resident, trace=True)
+    st["by_size"] = latency_by_size(tr)
+    return st
+
+
+def serving_rate_sweep(brev, arena, seconds):
+    """Poisson arrival rates of 20k..200k req/s for three servers -- the
+    launch loop with one request per launch, the loop with continuous
+    batching (up to 256 requests per launch), and the resident kernel -- on
+    the configured mix (k 10..24) and on small requests (k 10..16), E in
+    {4, 8, 16}.  Each point reports the sustained completions per second,
+    GB/s and latency; a server that cannot keep up completes fewer requests
+    per second than offered and its latency grows with the backlog."""
+    servers = (("launch_one_per_launch", dict(resident=False, max_batch=1)),
+               ("launch_batched", dict(resident=False, max_batch=256)),
+               ("resident", dict(resident=True)))
+    out = {"seconds_per_point": seconds, "points": {}}
+    for mix, kr in (("mix_k10-24", (10, 24)), ("small_k10-16", (10, 16))):
+        for rate in (20000.0, 50000.0, 100000.0, 200000.0):
+            for name, kw in servers:
+                st, _ = brev.brev_server_run_poisson(arena, seed=6, rate_per_s=rate,
+                                                     seconds=seconds, k_range=kr, **kw)
+                out["points"][f"{mix}_{int(rate / 1000)}k_{name}"] = {
+                    "offered_req_per_s": rate,
+                    "completed_req_per_s": round(st["req_per_s"], 1),
+                    "gbs": round(st["gbs"], 1),
+                    "p50_us": round(st["p50_us"], 1), "p99_us": round(st["p99_us"], 1),
+                    "max_us": round(st["max_us"], 1),
+                    "mean_batch": round(st["completed"] / max(1, st["batches"]), 2),
+                    "launches": st["launches"]}
     return out
 
 
@@ -737,11 +946,44 @@ def bench_e2e(torch, brev, inputs, pts, seq, steps, stream, sampler, reduce_max,
     el = reduce_max(time.perf_counter() - t0)
     sampler.window(w0, time.time())
     step_bytes = sum(p["bytes"] for p, _ in seq)
-    return {"value": round(ws * step_bytes * steps / el / 1e9, 1), "unit": "GB/s",
+    value = ws * step_bytes * steps / el / 1e9
+    # the link's ceiling for the same traffic, measured the same way: every
+    # point's input copied host -> device on one stream while its size in
+    # results goes device -> host on another (cudaMemcpyAsync through torch,
+    # page-locked buffers), host clock around each step
+    s_in = torch.cuda.Stream(stream.device)
+    s_out = torch.cuda.Stream(stream.device)
+
+    def link_step():
+        with torch.cuda.stream(s_in):
+            for p, _ in seq:
+                nb = p["src"].numel()
+                p["dst"].copy_(host_src[p["kind"]][:nb], non_blocking=True)
+        with torch.cuda.stream(s_out):
+            for p, _ in seq:
+                nb = p["src"].numel()
+                host_dst[:nb].copy_(p["src"], non_blocking=True)
+        s_in.synchronize()
+        s_out.synchronize()
+
+    link_step()
+    barrier()
+    w0 = time.time()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        link_step()
+    barrier()
+    el_link = reduce_max(time.perf_counter() - t0)
+    sampler.window(w0, time.time())
+    link = ws * step_bytes * steps / el_link / 1e9
+    return {"value": round(value, 1), "unit": "GB/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d, "steps": steps,
             "api": "brev_permute_host on page-locked host buffers: the kernel reads each "
                    "input from and writes each result to host memory over NVLink-C2C, "
-                   "every point every step, host clock around the calls"}
+                   "every point every step, host clock around the calls",
+            "link_gbs": round(link, 1), "frac": round(value / link, 4),
+            "link_from": "the same bytes moved by concurrent host->device and device->host "
+                         "cudaMemcpyAsync (two streams, page-locked buffers), host clock"}
 
 
 # --------------------------------------------------------- CPU baseline --
@@ -850,7 +1092,7 @@ def run_reference(args):
             "impl": "reference", "value": round(value, 3), "unit": "GB/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(secs / args.steps * 1e3, 3), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_LABEL,
             "data": "synthetic (seeded SplitMix64)",
             "config": sweep_config(args.kmax, args.kinds, ws, reference_l2_mib()),
             "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": 1,

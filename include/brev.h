@@ -129,7 +129,7 @@ BREV_API void brev_plan_destroy(brev_plan *plan);
  * fragmentation, is not acceptable.  Same arguments and result as
  * brev_permute_batched_mixed, but the call allocates nothing: its scratch
  * (ticket counter and per-array descriptors) is a fixed device array inside
- * the library of 256 + BREV_NOALLOC_MAX_ARRAYS * 40 bytes (about 41 KiB),
+ * the library of 256 + BREV_NOALLOC_MAX_ARRAYS * 48 bytes (about 48 KiB),
  * which every GPU that loads the library holds until the process exits.
  *   - count > BREV_NOALLOC_MAX_ARRAYS returns BREV_ERR_INVALID_ARG.
  *   - The first call on a device looks up the array's device address (once
@@ -146,6 +146,58 @@ BREV_API void brev_plan_destroy(brev_plan *plan);
 BREV_API brev_status brev_permute_batched_noalloc(void *const *ptr_array, const int *log2n_array,
                                                   const int *elem_bytes_array, int count,
                                                   void *stream);
+
+/* ------------------------------------------- one array over several GPUs */
+
+/* The permutation of one array of 2^log2n elements held by G = 2^log2_ranks
+ * ranks (one GPU each), rank p holding the consecutive block of elements
+ * [p 2^(log2n - log2_ranks), (p + 1) 2^(log2n - log2_ranks)).  By the
+ * concatenation identity of the paper's Introduction (rev(x y z) =
+ * rev(z) rev(y) rev(x)), element (p, m, l) -- rank, middle and low log2_ranks
+ * bits of its index -- goes to rank rev(l) at local offset
+ * rev(m) 2^log2_ranks + rev(p).  Three steps per rank, each block of
+ * 2^(log2n - log2_ranks) elements:
+ *   1. brev_dist_pack: a local pass into the send buffer, whose segment q
+ *      (2^(log2n - 2 log2_ranks) elements) is what rank q needs;
+ *   2. the caller's exchange: segment q of every rank p's send buffer to
+ *      segment p of rank q's receive buffer (an all-to-all of equal parts;
+ *      brev_dist_plan gives the offsets in elements);
+ *   3. brev_dist_finish: a local pass from the receive buffer into the
+ *      block, which then holds the block's part of the permuted array.
+ * Constraints: 2 log2_ranks <= log2n, blocks of at most 2^34 elements,
+ * log2_ranks <= BREV_DIST_MAX_LOG2_RANKS and, for the finish, at most 5
+ * (16-byte elements), 5 (8), 6 (4), 7 (2), 8 (1).  Buffers are device
+ * memory of the calling rank's current device, aligned to elem_bytes.
+ * Errors: BREV_ERR_INVALID_ARG, BREV_ERR_ALIGNMENT, BREV_ERR_OVERLAP,
+ * BREV_ERR_UNSUPPORTED, BREV_ERR_CUDA, as brev_permute_to. */
+#define BREV_DIST_MAX_LOG2_RANKS 10
+
+/* Offsets (in elements) of the exchange on rank `rank`: segment q of the
+ * send buffer starts at send_offsets[q] and goes to rank q; the segment
+ * from rank q lands at recv_offsets[q]; every segment holds
+ * *segment_elems elements.  send_offsets and recv_offsets hold
+ * 2^log2_ranks entries.  Host-only (no GPU needed). */
+BREV_API brev_status brev_dist_plan(int log2n, int log2_ranks, int elem_bytes, int rank,
+                                    uint64_t *send_offsets, uint64_t *recv_offsets,
+                                    uint64_t *segment_elems);
+/* Step 1: send = the (log2n - log2_ranks)-bit permutation of block (send may
+ * equal block: in place). */
+BREV_API brev_status brev_dist_pack(void *send, const void *block, int log2n, int log2_ranks,
+                                    int elem_bytes, void *stream);
+/* Step 3: block[r 2^log2_ranks + rev(p)] = recv[p 2^(log2n - 2 log2_ranks) + r]
+ * (a transposition with the rows taken in bit-reversed order); block and
+ * recv must not overlap. */
+BREV_API brev_status brev_dist_finish(void *block, const void *recv, int log2n, int log2_ranks,
+                                      int elem_bytes, void *stream);
+
+/* A batch of independent arrays split across `world` ranks by array: owner[i]
+ * receives the rank that permutes array i.  Arrays go largest first to the
+ * rank with the fewest bytes so far, so every rank's share of the bytes is
+ * within one array of the mean.  Host-only; the same inputs give the same
+ * owners on every rank (no communication needed).  Errors:
+ * BREV_ERR_INVALID_ARG. */
+BREV_API brev_status brev_shard_batch(const int *log2n_array, const int *elem_bytes_array,
+                                      int count, int world, int *owner);
 
 /* ---------------------------------------------------------------- transpositions */
 
@@ -282,6 +334,8 @@ typedef struct brev_server_request {
                                             * when resident), done: completion on
                                             * the device clock (launches) or seen
                                             * by the serving thread (resident) */
+    double seen_us; /* completion seen by the serving thread (both modes): the
+                     * latency p50_us / p99_us count, seen_us - arrival_us */
 } brev_server_request;
 
 BREV_API brev_status brev_server_create(const brev_server_config *cfg, void *arena,
@@ -391,9 +445,26 @@ typedef struct brev_device_info {
 /* Properties of the current device (needs a GPU). */
 BREV_API brev_status brev_get_device_info(brev_device_info *out);
 
+/* Measured FP64 fused multiply-add rate of the current device, in TFLOP/s
+ * (2 flops per FMA): the ceiling of the complex<double> FFT stages of
+ * brev_fft_stages, whose time is their FP64 arithmetic.  The paper has no
+ * counterpart; it is the denominator of that roofline.  Runs a kernel of
+ * independent FMA chains on every SM for about 10 ms, four times on a
+ * stream of its own, and returns the best of the last three; blocks the
+ * calling thread.  Errors: BREV_ERR_INVALID_ARG (NULL), BREV_ERR_CUDA. */
+BREV_API brev_status brev_fp64_fma_tflops(double *tflops);
+
 /* Number of kernel launches the library has issued on this process (all
  * entry points); lets callers count launches inside a timed region. */
 BREV_API uint64_t brev_launch_count(void);
+
+/* Device memory of the library's workspace pool on the current device:
+ * *reserved = bytes the pool holds from the device, *used = bytes of it in
+ * use by work not yet released (both 0 before the first call that needs
+ * workspace on this device).  The pool keeps up to 32 MiB reserved across
+ * synchronisations.  Host-side query; it creates nothing.  Errors:
+ * BREV_ERR_INVALID_ARG (a NULL output), BREV_ERR_CUDA. */
+BREV_API brev_status brev_workspace_bytes(uint64_t *reserved, uint64_t *used);
 
 /* Number of times a CTA of the batched kernel gave up waiting for its own
  * bulk copies into shared memory (about one second with the copies not

@@ -57,7 +57,7 @@ class ServerRequest(ctypes.Structure):
     _fields_ = [("offset", ctypes.c_uint64), ("log2n", ctypes.c_int),
                 ("elem_bytes", ctypes.c_int), ("batch", ctypes.c_int),
                 ("arrival_us", ctypes.c_double), ("launch_us", ctypes.c_double),
-                ("done_us", ctypes.c_double)]
+                ("done_us", ctypes.c_double), ("seen_us", ctypes.c_double)]
 
 
 SIGNATURES = {
@@ -71,6 +71,11 @@ SIGNATURES = {
     "brev_plan_destroy": (None, [_vp]),
     "brev_permute_host": (_i, [_vp, _vp, _i, _i, _vp]),
     "brev_transpose": (_i, [_vp, _vp, _i, _i, _i, _vp]),
+    "brev_dist_plan": (_i, [_i, _i, _i, _i, ctypes.POINTER(_u64), ctypes.POINTER(_u64),
+                            ctypes.POINTER(_u64)]),
+    "brev_dist_pack": (_i, [_vp, _vp, _i, _i, _i, _vp]),
+    "brev_dist_finish": (_i, [_vp, _vp, _i, _i, _i, _vp]),
+    "brev_shard_batch": (_i, [_ip, _ip, _i, _i, _ip]),
     "brev_even_odd": (_i, [_vp, _vp, _i, _i, _vp]),
     "brev_perfect_shuffle": (_i, [_vp, _vp, _i, _i, _vp]),
     "brev_permute_segments": (_i, [_vp, _i, _i, _i, _vp]),
@@ -90,7 +95,9 @@ SIGNATURES = {
     "brev_load_tune_cache": (_i, [_cp]),
     "brev_reset_tuning": (None, []),
     "brev_get_device_info": (_i, [ctypes.POINTER(DeviceInfo)]),
+    "brev_fp64_fma_tflops": (_i, [ctypes.POINTER(ctypes.c_double)]),
     "brev_launch_count": (_u64, []),
+    "brev_workspace_bytes": (_i, [ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
     "brev_wait_timeouts": (_i, [ctypes.POINTER(_u64)]),
     "brev_status_string": (_cp, [_i]),
     "brev_last_error": (_cp, []),
@@ -285,6 +292,86 @@ def brev_transpose(dst, src, log2_rows: int, log2_cols: int, stream=None) -> Non
            "brev_transpose")
 
 
+# ------------------------------------------------- one array, G ranks --
+def brev_dist_plan(log2n: int, log2_ranks: int, elem_bytes: int, rank: int):
+    """(send_offsets, recv_offsets, segment_elems) of the exchange on rank
+    `rank` (offsets in elements, one per peer); host-only."""
+    G = 1 << log2_ranks
+    so, ro, seg = (ctypes.c_uint64 * G)(), (ctypes.c_uint64 * G)(), ctypes.c_uint64()
+    _check(lib().brev_dist_plan(log2n, log2_ranks, elem_bytes, rank, so, ro, ctypes.byref(seg)),
+           "brev_dist_plan")
+    return list(so), list(ro), seg.value
+
+
+def brev_dist_pack(send, block, log2n: int, log2_ranks: int, stream=None) -> None:
+    """Step 1 of the permutation over 2^log2_ranks ranks (send may be block)."""
+    _flat(send), _flat(block)
+    _check(lib().brev_dist_pack(send.data_ptr(), block.data_ptr(), log2n, log2_ranks,
+                                block.element_size(), _stream_handle(stream, block.device)),
+           "brev_dist_pack")
+
+
+def brev_dist_finish(block, recv, log2n: int, log2_ranks: int, stream=None) -> None:
+    """Step 3 of the permutation over 2^log2_ranks ranks."""
+    _flat(block), _flat(recv)
+    _check(lib().brev_dist_finish(block.data_ptr(), recv.data_ptr(), log2n, log2_ranks,
+                                  block.element_size(), _stream_handle(stream, block.device)),
+           "brev_dist_finish")
+
+
+def dist_steps(block, recv, log2n: int, log2_ranks: int, rank: int, pack, exchange, finish):
+    """The three steps on one rank, with the local passes and the exchange
+    passed in: pack(block) permutes the block in place into send order,
+    exchange(recv, send, seg_elems) moves segment q of every rank's send
+    buffer to segment p = sender of rank q's receive buffer (equal
+    segments, offsets from brev_dist_plan), finish(block, recv) writes the
+    result.  brev_permute_distributed passes the library's kernels and
+    torch.distributed's all-to-all."""
+    E = block.element_size()
+    so, ro, seg = brev_dist_plan(log2n, log2_ranks, E, rank)
+    G = 1 << log2_ranks
+    if so != [q * seg for q in range(G)] or ro != so:
+        raise RuntimeError("exchange plan is not one of equal consecutive segments")
+    pack(block)
+    exchange(recv, block, seg)
+    finish(block, recv)
+
+
+def brev_permute_distributed(block, recv=None, group=None, stream=None) -> None:
+    """Permute one array spread over the ranks of `group` (a power of two of
+    them, one GPU each), rank p holding the p-th consecutive block: on
+    return every rank's block holds its part of the permuted array.  recv
+    is a scratch tensor like block (allocated when None).  The exchange is
+    torch.distributed's all-to-all (NCCL on GPUs)."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    g = _log2(world)
+    rank = dist.get_rank(group)
+    log2n = _log2(block.numel()) + g
+    if recv is None:
+        recv = torch.empty_like(block)
+
+    def exchange(r, s, seg):
+        dist.all_to_all_single(r.view(torch.uint8), s.view(torch.uint8), group=group)
+
+    dist_steps(block, recv, log2n, g, rank,
+               pack=lambda b: brev_dist_pack(b, b, log2n, g, stream),
+               exchange=exchange,
+               finish=lambda b, r: brev_dist_finish(b, r, log2n, g, stream))
+
+
+def brev_shard_batch(log2n: Sequence[int], elem_bytes: Sequence[int], world: int) -> list[int]:
+    """Owner rank of each array of a batch split across `world` ranks by
+    array (largest first, to the least-loaded rank); host-only."""
+    n = len(log2n)
+    ks = (ctypes.c_int * n)(*log2n)
+    es = (ctypes.c_int * n)(*elem_bytes)
+    own = (ctypes.c_int * n)()
+    _check(lib().brev_shard_batch(ks, es, n, world, own), "brev_shard_batch")
+    return list(own)
+
+
 def brev_even_odd(dst, src, stream=None) -> None:
     """Even-indexed elements, then odd-indexed ones (the Stockham step)."""
     _flat(dst), _flat(src)
@@ -363,7 +450,7 @@ def brev_server_run_poisson(arena, seed: int, rate_per_s: float, seconds: float,
     if trace:
         recs = [{"offset": r.offset, "log2n": r.log2n, "elem_bytes": r.elem_bytes,
                  "batch": r.batch, "arrival_us": r.arrival_us, "launch_us": r.launch_us,
-                 "done_us": r.done_us}
+                 "done_us": r.done_us, "seen_us": r.seen_us}
                 for r in tr[:st.offered]]
     return stats, recs
 
@@ -430,8 +517,23 @@ def brev_get_device_info() -> dict:
             "nominal_gbs": info.nominal_gbs, "max_smem_per_block": info.max_smem_per_block}
 
 
+def brev_fp64_fma_tflops() -> float:
+    """Measured FP64 fused multiply-add rate of the current device (TFLOP/s)."""
+    v = ctypes.c_double()
+    _check(lib().brev_fp64_fma_tflops(ctypes.byref(v)), "brev_fp64_fma_tflops")
+    return v.value
+
+
 def brev_launch_count() -> int:
     return int(lib().brev_launch_count())
+
+
+def brev_workspace_bytes() -> tuple[int, int]:
+    """(reserved, used) bytes of the library's workspace pool on the
+    current device."""
+    r, u = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().brev_workspace_bytes(ctypes.byref(r), ctypes.byref(u)), "brev_workspace_bytes")
+    return r.value, u.value
 
 
 def brev_wait_timeouts() -> int:

@@ -147,6 +147,12 @@ int tuned_batched_stages(int k, int E);
 int tuned_batched_copy(int k, int E);
 // Argument checks of a batch (sizes, alignment, device ranges, no overlap).
 brev_status validate_batch_items(const BatchItem* items, int count);
+// Transposition of a 2^g x 2^c matrix whose source row x becomes
+// destination column rev_g(x) (out of place, no argument checks), and the
+// largest g it takes for element size E (brev_transpose.cu).
+brev_status transpose_rowrev_launch(void* dst, const void* src, int g, int c, int E,
+                                    cudaStream_t stream);
+int transpose_rowrev_max_g(int E);
 // Launch one permutation without argument checks (src == dst: in-place).
 brev_status launch_single(void* dst, const void* src, int k, int E, cudaStream_t stream);
 // Load the kernel that launch_single would use for (k, E, in place) -- with

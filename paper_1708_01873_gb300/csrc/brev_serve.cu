@@ -186,6 +186,7 @@ void finish_stats(const std::vector<Req>& reqs, const std::vector<double>& lat_u
       trace[i].arrival_us = reqs[i].arrival * 1e6;
       trace[i].launch_us = reqs[i].launch * 1e6;
       trace[i].done_us = reqs[i].done * 1e6;
+      trace[i].seen_us = reqs[i].seen * 1e6;
     }
   }
 }

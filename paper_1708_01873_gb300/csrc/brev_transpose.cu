@@ -40,6 +40,25 @@ __global__ void __launch_bounds__(TR_THREADS)
   store_tile_g<E, W, TR_THREADS, false>(sm, d, (uint64_t)E << a, bx, bz);
 }
 
+// Out-of-place transposition of a 2^bx x 2^c matrix (one tile row spans
+// every row) whose source row x becomes destination column rev_bx(x):
+// dst[j 2^bx + rev(x)] = src[x 2^c + j].  The last local pass of the
+// permutation spread over 2^bx ranks (brev_dist_finish).
+template <int E, int W>
+__global__ void __launch_bounds__(TR_THREADS)
+    k_transpose_rowrev(char* __restrict__ dst, const char* __restrict__ src, int c, int bx,
+                       int bz) {
+  extern __shared__ uint4 smem_u4[];
+  auto* sm = reinterpret_cast<typename ChunkT<W>::type*>(smem_u4);
+  pdl_enter();
+  const uint64_t tc = blockIdx.x;
+  const char* s = src + (tc << bz) * E;
+  char* d = dst + (tc << (bz + bx)) * E;
+  load_tiles_g<E, W, TR_THREADS, true, true>(sm, s, nullptr, (uint64_t)E << c, 1, bx, bz);
+  __syncthreads();
+  store_tile_g<E, W, TR_THREADS, false>(sm, d, (uint64_t)E << bx, bx, bz);
+}
+
 template <int E, int W>
 __global__ void __launch_bounds__(TR_THREADS) k_transpose_inplace(char* data, int a, int b) {
   extern __shared__ uint4 smem_u4[];
@@ -94,12 +113,13 @@ struct TrKernels {
   const void* oop;
   const void* inplace;
   const void* seg;
+  const void* rowrev;
 };
 
 template <int E, int W>
 static TrKernels tr_kernels() {
   return {(const void*)&k_transpose<E, W>, (const void*)&k_transpose_inplace<E, W>,
-          (const void*)&k_segments<E, W>};
+          (const void*)&k_segments<E, W>, (const void*)&k_transpose_rowrev<E, W>};
 }
 
 static bool tr_lookup(int E, int W, TrKernels* out) {
@@ -189,6 +209,30 @@ static brev_status transpose_launch(void* dst, const void* src, int a, int c, in
   void* args[] = {(void*)&d, (void*)&s, (void*)&a, (void*)&c, (void*)&bx, (void*)&bz};
   return launch(K.oop, grid, smem, args, stream, "transposition launch");
 }
+
+// Transposition of a 2^g x 2^c matrix with source row x written to
+// destination column rev_g(x), without argument checks; g <= the tile's
+// row exponent (every tile spans all rows).
+brev_status transpose_rowrev_launch(void* dst, const void* src, int g, int c, int E,
+                                    cudaStream_t stream) {
+  const bool vec16 = (((uintptr_t)dst | (uintptr_t)src) % 16) == 0;
+  const int V = 16 / E, lv = ilog2i(V);
+  const int B = target_b(E), T = 2 * B;
+  if (g > B) return set_error(BREV_ERR_UNSUPPORTED, "2^%d rows exceed one tile", g);
+  const int bz = std::min(c, T - g);
+  const int W = (vec16 && g >= lv && bz >= lv) ? 16 : E;
+  TrKernels K;
+  if (!tr_lookup(E, W, &K)) return set_error(BREV_ERR_UNSUPPORTED, "no kernel");
+  const unsigned long long grid = 1ull << (c - bz);
+  const unsigned smem = (unsigned)E << (g + bz);
+  char* d = (char*)dst;
+  const char* s = (const char*)src;
+  int gg = g;
+  void* args[] = {(void*)&d, (void*)&s, (void*)&c, (void*)&gg, (void*)&bz};
+  return launch(K.rowrev, grid, smem, args, stream, "row-reversed transposition launch");
+}
+
+int transpose_rowrev_max_g(int E) { return target_b(E); }
 
 // Segmented bit reversal without argument checks: 2^s segments of 2^m.
 static brev_status segments_launch(void* data, int s_log, int m, int E, cudaStream_t stream) {

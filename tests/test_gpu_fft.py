@@ -11,6 +11,16 @@ per component is below (S + 1) * 8 * eps * 2^S, with eps = 2^-24 for
 complex<float> (float arithmetic; the oracle is exact to 2^-53 by
 comparison) and 2^-53 for complex<double>.  Zero stages are the plain
 permutation and must match bit for bit.
+
+The constant butterflies (twiddles 1, -i and the eighth turns (+-1 - i)/sqrt 2,
+used in the first pass and in the second pass's groups j = 0 and j = 4) stay
+inside the same per-stage allowance: an eighth-turn product is one rounded
+sum of the two components (|sum| <= 2^s), scaled by sqrt(1/2) inside a
+multiply-add that adds a (one rounding, |a'| <= 2^s sqrt 2), then
+b' = 2a - a' (one more), i.e. under (0.36 + 0.71 + 0.71) eps 2^s per
+component against the 4 eps 2^s sqrt 2 = 5.66 eps 2^s allowed per stage;
+the rounding of sqrt(1/2) itself adds 2^-54 relative (complex<double>) or
+2^-25 (complex<float>), far inside the rest.  1 and -i are exact.
 """
 import numpy as np
 import pytest
@@ -61,6 +71,29 @@ def test_fused_stages_vs_oracle(brev_lib, oracle_lib, cuda_device, E):
                         brev_lib.brev_fft_stages(out, src, S, inverse)
                     check(to_bytes(out), x, k, E, S, inverse,
                           f"k={k} S={S} E={E} inplace={inplace} inverse={inverse}")
+
+
+@pytest.mark.parametrize("E,S", [(8, 6), (16, 5)])
+def test_eighth_turn_groups_both_directions(brev_lib, oracle_lib, cuda_device, E, S):
+    """The largest stage count of each element size (6 for complex<float>,
+    5 for complex<double>) runs the second pass's j = 0 and j = 4 groups on
+    the compile-time butterflies; the inverse conjugates around them.  Both
+    directions, in and out of place, several sizes, against the oracle
+    within the derived tolerance."""
+    for k in (S, 10, 13, 16, 19, 22):
+        for inplace in (False, True):
+            for inverse in (True, False):
+                seed = 9000 + 10 * k + E + 2 * inverse + inplace
+                src = device_array(seed, k, E)
+                x = as_complex(host_array(seed, k, E), E)
+                if inplace:
+                    brev_lib.brev_fft_stages(src, src, S, inverse)
+                    out = src
+                else:
+                    out = torch.empty_like(src)
+                    brev_lib.brev_fft_stages(out, src, S, inverse)
+                check(to_bytes(out), x, k, E, S, inverse,
+                      f"k={k} S={S} E={E} inplace={inplace} inverse={inverse}")
 
 
 @pytest.mark.parametrize("E", (8, 16))

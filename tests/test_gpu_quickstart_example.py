@@ -1,9 +1,9 @@
-"""The README's Python example runs as written on the GPU and does what it
-says: y (out of place) equals x permuted in place, and the batched call
-followed by one plan replay applies the involution twice, restoring the
-arrays."""
+"""The quick-start example (examples/quickstart.py) runs as written on the
+GPU and does what it says: y (out of place) equals x permuted in place, and
+the batched call followed by one plan replay applies the involution twice,
+restoring the arrays."""
 import os
-import re
+import runpy
 
 import pytest
 import torch
@@ -13,12 +13,8 @@ pytestmark = pytest.mark.gpu
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def test_readme_python_example(brev_lib, cuda_device):
-    with open(os.path.join(ROOT, "README.md")) as f:
-        blocks = re.findall(r"```python\n(.*?)```", f.read(), re.S)
-    assert len(blocks) == 1
+def test_quickstart_example(brev_lib, cuda_device):
     torch.manual_seed(0)
-    ns = {}
     real_randn = torch.randn
     originals = []
 
@@ -29,7 +25,7 @@ def test_readme_python_example(brev_lib, cuda_device):
 
     torch.randn = recording_randn
     try:
-        exec(compile(blocks[0], "README.md", "exec"), ns)
+        ns = runpy.run_path(os.path.join(ROOT, "examples", "quickstart.py"))
         torch.cuda.synchronize()
     finally:
         torch.randn = real_randn
