@@ -384,7 +384,7 @@ def run_brev(args):
     if not args.no_batched:
         batched = section("batched", lambda: bench_batched(
             torch, brev, inputs, device, stream, sampler, reduce_max, barrier,
-            count=args.batch_count, kmax=args.batch_kmax))
+            count=args.batch_count, kmax=args.batch_kmax, ws=ws, rank=rank))
 
     # ------------------------------------- large single arrays (cfg 3)
     large_cfg = None
@@ -406,6 +406,12 @@ def run_brev(args):
         next_rows = section("next", lambda: bench_next(
             torch, brev, inputs, device, stream, sampler, reduce_max, barrier, peak,
             k=args.next_k))
+
+    # -------------------------- one array over all ranks (N > 1 only)
+    distributed = None
+    if ws > 1:
+        distributed = section("distributed", lambda: bench_distributed(
+            torch, brev, device, stream, sampler, reduce_max, barrier, ws, rank))
 
     # ------------------------------------------------------------ e2e
     e2e = None
@@ -482,6 +488,7 @@ def run_brev(args):
             "serving": serving,
             "large_single_arrays": large_cfg,
             "midsize_back_to_back": midsize,
+            "distributed_single_array": distributed,
             "transpositions_and_recursive": next_rows,
             "e2e": e2e,
             "gpu_launches": int(launches),
@@ -686,6 +693,60 @@ def bench_midsize(torch, brev, device, stream, sampler, reduce_max, barrier, pea
     return out
 
 
+def bench_distributed(torch, brev, device, stream, sampler, reduce_max, barrier, ws, rank,
+                      log2_block=27, reps=5, warm=2):
+    """One complex<double> array of ws x 2^27 elements (2 GiB per rank)
+    spread over the ranks: pack (local pass), all-to-all (NCCL), finish
+    (local pass), timed on the launch stream with a barrier on both sides,
+    max over ranks.  Runs only with a power-of-two number of ranks."""
+    import torch.distributed as dist
+    g = ws.bit_length() - 1
+    if ws != 1 << g:
+        return {"skipped": f"{ws} ranks is not a power of two"}
+    E = 16
+    k = log2_block + g
+    block = torch.empty((1 << log2_block) * E, dtype=torch.uint8, device=device)
+    block.fill_(rank & 0xFF)
+    recv = torch.empty_like(block)
+    blk = block.view(torch.complex128)
+    rcv = recv.view(torch.complex128)
+    L = brev.lib()
+    sh = stream.cuda_stream
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        brev.brev_dist_pack(blk, blk, k, g, stream)
+        if ev:
+            ev[1].record(stream)
+        dist.all_to_all_single(recv, block)
+        if ev:
+            ev[2].record(stream)
+        brev.brev_dist_finish(blk, rcv, k, g, stream)
+        if ev:
+            ev[3].record(stream)
+
+    for _ in range(warm):
+        step()
+    barrier()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(reps)]
+    w0 = time.time()
+    for e in evs:
+        step(e)
+    barrier()
+    sampler.window(w0, time.time())
+    tot = reduce_max(evs[0][0].elapsed_time(evs[-1][3])) / reps
+    pack = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    a2a = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+    fin = statistics.mean(e[2].elapsed_time(e[3]) for e in evs)
+    nbytes = 2 * (E << k)  # the whole array read and written once
+    return {"workload": f"complex<double>, k={k} over {ws} ranks (2^{log2_block} elements each)",
+            "ms_per_step": round(tot, 4), "gbs": round(nbytes / (tot * 1e-3) / 1e9, 1),
+            "rank0_pack_ms": round(pack, 4), "rank0_all_to_all_ms": round(a2a, 4),
+            "rank0_finish_ms": round(fin, 4),
+            "exchange": "torch.distributed.all_to_all_single (NCCL), equal segments"}
+
+
 def bench_next(torch, brev, inputs, device, stream, sampler, reduce_max, barrier, peak,
                reps=5, warm=2, k=28):
     """The widened rows: transpositions (square and narrow: the even-odd step
@@ -828,18 +889,31 @@ def serving_rate_sweep(brev, arena, seconds):
 
 
 def bench_batched(torch, brev, inputs, device, stream, sampler, reduce_max, barrier,
-                  reps=10, warm=3, count=4096, kmax=20):
+                  reps=10, warm=3, count=4096, kmax=20, ws=1, rank=0):
+    """The 4096-array batch: one persistent launch (as a captured plan, and
+    per call) against a loop of single-array launches (plain and captured).
+    With several ranks the batch is split across them by array
+    (brev_shard_batch: strong scaling, each rank launches its share) and
+    GB/s counts the whole batch over the slowest rank's time."""
     import numpy as np
     rng = np.random.default_rng(4)
     ks = rng.integers(8, kmax + 1, size=count)
     Es = rng.choice([8, 16], size=count)
+    owner = (brev.brev_shard_batch([int(x) for x in ks], [int(x) for x in Es], ws)
+             if ws > 1 else [0] * count)
     arrays = []
+    kept = []
     for i in range(count):
+        if owner[i] != rank:
+            continue
         E = int(Es[i])
         a = torch.empty((1 << int(ks[i])) * E, dtype=torch.uint8, device=device)
         inputs.fill_torch(a, 40000 + i, "c64" if E == 8 else "c128", chunk=1 << 26)
         arrays.append(a.view(torch.complex64 if E == 8 else torch.complex128))
-    total = sum(2 * a.numel() * a.element_size() for a in arrays)
+        kept.append(i)
+    total = sum(2 * (int(E) << int(k)) for k, E in zip(ks, Es))  # the whole batch
+    ks = ks[kept]
+    Es = Es[kept]
     L = brev.lib()
     sh = stream.cuda_stream
     plan = brev.BrevPlan(arrays)
@@ -892,6 +966,8 @@ def bench_batched(torch, brev, inputs, device, stream, sampler, reduce_max, barr
                       for k in range(8, kmax + 1)})
     res = {"workload": f"{count} arrays, k uniform in [8,{kmax}], E uniform in {{8,16}} "
                        "(seed 4), in place; persistent = one launch per batch",
+           "sharding": (f"{ws} ranks by array (brev_shard_batch), strong scaling: "
+                        f"{len(kept)} arrays on rank 0") if ws > 1 else "1 GPU",
            "tile_exponent_b": {f"E{E}_k{k}": b for E, k, b in tuned_b},
            "tile_exponent_from": "autotuned table (brev_autotune, tune_gb300.json)",
            "bytes_per_batch": total, "launches_in_loop": int(loop_launches), **out,
@@ -975,15 +1051,26 @@ def bench_e2e(torch, brev, inputs, pts, seq, steps, stream, sampler, reduce_max,
     barrier()
     el_link = reduce_max(time.perf_counter() - t0)
     sampler.window(w0, time.time())
-    link = ws * step_bytes * steps / el_link / 1e9
+    ce = ws * step_bytes * steps / el_link / 1e9
+    # the route the permutation itself takes: SMs reading and writing
+    # page-locked host memory, measured as a plain copy kernel over the
+    # largest pair of buffers (4 GiB)
+    big = max(host_src, key=lambda kd: host_src[kd].numel())
+    w0 = time.time()
+    link = brev.brev_host_link_gbs(host_dst, host_src[big][:host_dst.numel()])
+    sampler.window(w0, time.time())
     return {"value": round(value, 1), "unit": "GB/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d, "steps": steps,
             "api": "brev_permute_host on page-locked host buffers: the kernel reads each "
                    "input from and writes each result to host memory over NVLink-C2C, "
                    "every point every step, host clock around the calls",
             "link_gbs": round(link, 1), "frac": round(value / link, 4),
-            "link_from": "the same bytes moved by concurrent host->device and device->host "
-                         "cudaMemcpyAsync (two streams, page-locked buffers), host clock"}
+            "link_from": "copy kernel reading and writing page-locked host memory over "
+                         "NVLink-C2C (brev_host_link_gbs, 4 GiB, read + write bytes, events)",
+            "copy_engine_gbs": round(ce, 1),
+            "copy_engine_from": "the same bytes moved by concurrent host->device and "
+                                "device->host cudaMemcpyAsync (two streams, page-locked "
+                                "buffers), host clock"}
 
 
 # --------------------------------------------------------- CPU baseline --

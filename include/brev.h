@@ -454,6 +454,18 @@ BREV_API brev_status brev_get_device_info(brev_device_info *out);
  * calling thread.  Errors: BREV_ERR_INVALID_ARG (NULL), BREV_ERR_CUDA. */
 BREV_API brev_status brev_fp64_fma_tflops(double *tflops);
 
+/* Measured rate (GB/s, read + write bytes) of a plain copy kernel that reads
+ * `bytes` of page-locked host memory at src_host and writes them to
+ * page-locked host memory at dst_host -- the same route the host-buffer
+ * permutation takes (the SMs load and store host memory over the CPU-GPU
+ * link) with no permutation: the ceiling of brev_permute_host.  The paper
+ * has no counterpart.  Both pointers 16-byte aligned, bytes a multiple of 16,
+ * no overlap.  Four copies on a stream of its own, best of the last three;
+ * blocks the calling thread.  Errors: BREV_ERR_INVALID_ARG (NULL, not
+ * page-locked), BREV_ERR_ALIGNMENT, BREV_ERR_OVERLAP, BREV_ERR_CUDA. */
+BREV_API brev_status brev_host_link_gbs(void *dst_host, const void *src_host, uint64_t bytes,
+                                        double *gbs);
+
 /* Number of kernel launches the library has issued on this process (all
  * entry points); lets callers count launches inside a timed region. */
 BREV_API uint64_t brev_launch_count(void);

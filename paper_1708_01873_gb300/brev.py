@@ -96,6 +96,7 @@ SIGNATURES = {
     "brev_reset_tuning": (None, []),
     "brev_get_device_info": (_i, [ctypes.POINTER(DeviceInfo)]),
     "brev_fp64_fma_tflops": (_i, [ctypes.POINTER(ctypes.c_double)]),
+    "brev_host_link_gbs": (_i, [_vp, _vp, _u64, ctypes.POINTER(ctypes.c_double)]),
     "brev_launch_count": (_u64, []),
     "brev_workspace_bytes": (_i, [ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
     "brev_wait_timeouts": (_i, [ctypes.POINTER(_u64)]),
@@ -521,6 +522,18 @@ def brev_fp64_fma_tflops() -> float:
     """Measured FP64 fused multiply-add rate of the current device (TFLOP/s)."""
     v = ctypes.c_double()
     _check(lib().brev_fp64_fma_tflops(ctypes.byref(v)), "brev_fp64_fma_tflops")
+    return v.value
+
+
+def brev_host_link_gbs(dst_host, src_host) -> float:
+    """Measured rate (GB/s, read + write) of an SM-driven copy between two
+    page-locked host tensors of the same size: the host path's ceiling."""
+    v = ctypes.c_double()
+    nbytes = src_host.numel() * src_host.element_size()
+    if dst_host.numel() * dst_host.element_size() != nbytes:
+        raise ValueError("host tensors differ in size")
+    _check(lib().brev_host_link_gbs(dst_host.data_ptr(), src_host.data_ptr(), nbytes,
+                                    ctypes.byref(v)), "brev_host_link_gbs")
     return v.value
 
 
