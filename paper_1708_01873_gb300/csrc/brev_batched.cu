@@ -135,10 +135,13 @@ struct StageInfo {
   int E, b, k, nt;
   int rev;                    // 1: bit-reversed row and column maps, 0: identity
   // resident serving only: ring slot of the unit's request (-1 in a batch),
-  // the request's unit count and sequence number (completion accounting)
+  // the request's unit count and sequence number (completion accounting),
+  // and the units this CTA completes for the request with this unit (its
+  // ticket's units when this is the ticket's last unit, else 0)
   int slot;
   unsigned req_units;
   unsigned long long seq;
+  unsigned count;
 };
 
 __host__ __device__ constexpr unsigned padded_row_bytes(int E, int b) {
@@ -162,7 +165,7 @@ __device__ unsigned g_batched_wait_timeouts;
 // the row copies, which complete on `full`.
 __device__ __forceinline__ void issue_unit(const BatchDesc& d, unsigned u, StageInfo* info,
                                            unsigned char* buf, uint64_t* full, int slot = -1,
-                                           unsigned long long seq = 0) {
+                                           unsigned long long seq = 0, unsigned count = 0) {
   const int lane = threadIdx.x & 31;
   StageInfo s;
   s.E = d.E;
@@ -172,6 +175,7 @@ __device__ __forceinline__ void issue_unit(const BatchDesc& d, unsigned u, Stage
   s.slot = slot;
   s.req_units = d.units;
   s.seq = seq;
+  s.count = count;
   if (d.b == 0) {
     const uint32_t bytes = (uint32_t)d.E << d.k;
     s.a = s.r = d.ptr;
@@ -449,7 +453,7 @@ struct ServeCtl {  // device memory (256 bytes), zeroed before each launch
 static_assert(sizeof(ServeCtl) <= 256, "serving control block");
 struct ServeArgs {
   ServeDesc* d_ring;
-  unsigned* d_done;  // per slot: units completed, counted per consumer warp
+  unsigned* d_done;  // per slot: units completed, counted per ticket and CTA
   int* d_treq;       // ticket table: ticket & (ticket_table - 1) -> slot
   ServeCtl* ctl;
   const ServeHostReq* h_ring;
@@ -531,12 +535,47 @@ __device__ void serve_dispatch(const ServeArgs& A) {
   }
 }
 
+// A ticket taken by a producer, with its request's descriptor.
+struct ServeTicket {
+  BatchDesc d;
+  unsigned u, ulast;  // units [u, ulast) of the request
+  int slot;
+  unsigned long long seq;
+};
+
+// Read ticket t's request (ticket table, then device ring) into `x`; the
+// caller has acquired a published count above t.  Whole warp.
+__device__ __forceinline__ void serve_read_ticket(const ServeArgs& A, unsigned long long t,
+                                                  ServeTicket& x) {
+  __syncwarp();  // the lanes' reads below come after lane 0's acquire
+  // read through L2 (a slot's previous request may sit in this SM's L1)
+  const int sl = __ldcg(A.d_treq + (t & (A.ticket_table - 1)));
+  const ServeDesc* p = A.d_ring + sl;
+  BatchDesc& d = x.d;
+  d.ptr = (char*)__ldcg((const unsigned long long*)&p->ptr);
+  d.first_ticket = __ldcg(&p->first_ticket);
+  d.units = __ldcg(&p->units);
+  d.grain = __ldcg(&p->grain);
+  d.k = __ldcg(&p->k);
+  d.E = __ldcg(&p->E);
+  d.b = __ldcg(&p->b);
+  d.mode = BATCH_BITREV;
+  d.unit0 = 0;
+  d.copy = batched_copy_default(d.E, d.b);
+  x.seq = __ldcg(&p->seq);
+  x.slot = sl;
+  x.u = (unsigned)(t - d.first_ticket) * d.grain;
+  x.ulast = min(x.u + d.grain, d.units);
+  // the request's buffer may hold an earlier request's stores (generic
+  // proxy), made visible through the acquire chain; the copies that read it
+  // are async-proxy operations
+  fence_proxy_async_global();
+}
+
 // Producer: claim the next ticket and wait until it is published.
-// Returns 1 with (d, u, ulast, slot, seq) set, 0 at the end of the run,
-// -1 after idle_ns without it being published or the run ending.
-__device__ __forceinline__ int serve_next_ticket(const ServeArgs& A, BatchDesc& d, unsigned& u,
-                                                 unsigned& ulast, int& slot,
-                                                 unsigned long long& seq) {
+// Returns 1 with `x` set, 0 at the end of the run, -1 after idle_ns
+// without it being published or the run ending.
+__device__ __forceinline__ int serve_next_ticket(const ServeArgs& A, ServeTicket& x) {
   const int lane = threadIdx.x & 31;
   unsigned long long t = 0;
   int status = 0;
@@ -567,28 +606,7 @@ __device__ __forceinline__ int serve_next_ticket(const ServeArgs& A, BatchDesc& 
   status = __shfl_sync(0xffffffffu, status, 0);
   if (status <= 0) return status;
   t = __shfl_sync(0xffffffffu, t, 0);
-  __syncwarp();  // the lanes' reads below come after lane 0's acquire
-  // read through L2 (a slot's previous request may sit in this SM's L1)
-  const int sl = __ldcg(A.d_treq + (t & (A.ticket_table - 1)));
-  const ServeDesc* p = A.d_ring + sl;
-  d.ptr = (char*)__ldcg((const unsigned long long*)&p->ptr);
-  d.first_ticket = __ldcg(&p->first_ticket);
-  d.units = __ldcg(&p->units);
-  d.grain = __ldcg(&p->grain);
-  d.k = __ldcg(&p->k);
-  d.E = __ldcg(&p->E);
-  d.b = __ldcg(&p->b);
-  d.mode = BATCH_BITREV;
-  d.unit0 = 0;
-  d.copy = batched_copy_default(d.E, d.b);
-  seq = __ldcg(&p->seq);
-  slot = sl;
-  u = (unsigned)(t - d.first_ticket) * d.grain;
-  ulast = min(u + d.grain, d.units);
-  // the request's buffer may hold an earlier request's stores (generic
-  // proxy), made visible through the acquire chain; the copies that read it
-  // are async-proxy operations
-  fence_proxy_async_global();
+  serve_read_ticket(A, t, x);
   return 1;
 }
 
@@ -597,11 +615,13 @@ __global__ void __launch_bounds__(SERVE_BLOCK, BREV_BATCHED_MIN_CTAS)
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[BATCH_STAGES], empty[BATCH_STAGES];
   __shared__ StageInfo info[BATCH_STAGES];
+  __shared__ unsigned stored[BATCH_STAGES];  // consumer warps done with each stage, counted up
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) {
     for (int i = 0; i < BATCH_STAGES; ++i) {
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], BATCH_CONSUMER_WARPS);
+      stored[i] = 0;
     }
     mbar_init_fence();
   }
@@ -612,11 +632,10 @@ __global__ void __launch_bounds__(SERVE_BLOCK, BREV_BATCHED_MIN_CTAS)
     return;
   }
   if (warp == BATCH_CONSUMER_WARPS) {  // producer
-    int slot = -1;
-    unsigned u = 0, ulast = 0;
-    unsigned long long seq = 0;
-    BatchDesc d{};
-    unsigned i = 0;
+    ServeTicket cur;  // the ticket being run
+    cur.slot = -1;
+    cur.u = cur.ulast = 0;
+    unsigned i = 0, done_in_ticket = 0;
     bool ok = true, marker = false;
 #pragma unroll 1
     for (;; ++i) {
@@ -627,11 +646,12 @@ __global__ void __launch_bounds__(SERVE_BLOCK, BREV_BATCHED_MIN_CTAS)
         fence_proxy_async_smem();
       }
       int more = 1;
-      if (slot >= 0 && u + 1 < ulast) {
-        ++u;
+      if (cur.slot >= 0 && cur.u + 1 < cur.ulast) {
+        ++cur.u;
       } else {
-        more = serve_next_ticket(A, d, u, ulast, slot, seq);
+        more = serve_next_ticket(A, cur);
         if (more < 0) ok = false;
+        done_in_ticket = 0;
       }
       if (more <= 0) {  // end marker: a phase with no bytes
         if (lane == 0) {
@@ -641,7 +661,9 @@ __global__ void __launch_bounds__(SERVE_BLOCK, BREV_BATCHED_MIN_CTAS)
         marker = true;
         break;
       }
-      issue_unit(d, u, &info[st], smem + (size_t)st * A.stage_bytes, &full[st], slot, seq);
+      ++done_in_ticket;
+      issue_unit(cur.d, cur.u, &info[st], smem + (size_t)st * A.stage_bytes, &full[st],
+                 cur.slot, cur.seq, cur.u + 1 == cur.ulast ? done_in_ticket : 0u);
     }
     if (!ok && lane == 0) atomicAdd(&g_batched_wait_timeouts, 1u);
     // as in k_batched: the copies still in flight land before the CTA
@@ -670,15 +692,26 @@ __global__ void __launch_bounds__(SERVE_BLOCK, BREV_BATCHED_MIN_CTAS)
       case 8: store_staged_unit<8>(buf, s.a, s.r, s.stride, s.b, s.k, s.nt, s.rev); break;
       case 4: store_staged_unit<4>(buf, s.a, s.r, s.stride, s.b, s.k, s.nt, s.rev); break;
     }
-    // count the warp's share of the unit: the warp barrier orders every
-    // lane's stores before lane 0's release; the warp that completes the
-    // request has acquired all the others' and releases the lot to the host
+    // Completion accounting, one global atomic per ticket and CTA: each
+    // warp counts itself on the stage's shared counter (a release at CTA
+    // scope: its stores, ordered before by the warp barrier); the last of
+    // the 8 has acquired the others' and, on the ticket's last unit, adds
+    // the ticket's units to the request's count with a release at GPU
+    // scope, which covers every unit of the ticket (each warp stored them
+    // before this one).  The warp that completes the request has acquired
+    // all the others' and releases the lot to the host.  The stage is
+    // released first, so that the producer refills it while the GPU-scope
+    // release waits for the stores.  (One acquire-release atomic per warp
+    // per unit on the request's one counter -- 16 k on the same word for a
+    // 64 MiB request -- had held large requests near 5 TB/s.)
     __syncwarp();
     if (lane == 0) {
-      const unsigned need = (unsigned)BATCH_CONSUMER_WARPS * s.req_units;
-      if (atom_add_acq_rel_gpu(&A.d_done[s.slot], 1u) + 1u == need)
-        st_release_sys(&A.h_done[s.slot], s.seq + 1);
+      const bool last =
+          (atom_add_acq_rel_cta_shared(&stored[st], 1u) + 1u) % BATCH_CONSUMER_WARPS == 0;
       mbar_arrive(&empty[st]);
+      if (last && s.count > 0 &&
+          atom_add_acq_rel_gpu(&A.d_done[s.slot], s.count) + s.count == s.req_units)
+        st_release_sys(&A.h_done[s.slot], s.seq + 1);
     }
   }
 }
