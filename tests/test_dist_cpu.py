@@ -256,3 +256,22 @@ def test_shard_batch_balance():
             load[o] += E << k
         biggest = max(E << k for k, E in zip(ks, es))
         assert max(load) - min(load) <= biggest  # within one array of each other
+
+
+def test_latency_by_size_classes():
+    """The bench's per-size-class latency summary on a synthetic trace: the
+    slowest 1 % all in the large class, classes counted and split right,
+    requests never seen by the serving thread left out."""
+    sys.path.insert(0, ROOT)
+    import bench
+    trace = []
+    for i in range(1000):
+        k = 10 + (i % 15)                      # k 10..24
+        lat = 100.0 if k >= 23 and i % 7 == 0 else 10.0
+        trace.append({"log2n": k, "arrival_us": float(i), "seen_us": float(i) + lat})
+    trace.append({"log2n": 12, "arrival_us": 5.0, "seen_us": 0.0})  # never seen
+    out = bench.latency_by_size(trace)
+    assert sum(v["count"] for v in out.values()) == 1000
+    assert out["k23-24"]["share_of_slowest_1pct"] == 1.0
+    assert out["k10-16"]["p50_us"] == 10.0 and out["k23-24"]["p99_us"] == 100.0
+    assert bench.latency_by_size([]) is None
