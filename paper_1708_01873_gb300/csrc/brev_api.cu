@@ -296,6 +296,8 @@ static std::atomic<int8_t> g_tuned_batched[5][BREV_MAX_LOG2N + 1];
 static std::atomic<int8_t> g_tuned_batched_stages[5][BREV_MAX_LOG2N + 1];
 // tuned staging of the array's tile rows + 1 (0: not tuned)
 static std::atomic<int8_t> g_tuned_batched_copy[5][BREV_MAX_LOG2N + 1];
+// tuned consumer warps per CTA (0: not tuned)
+static std::atomic<int8_t> g_tuned_batched_warps[5][BREV_MAX_LOG2N + 1];
 static double g_tuned_batched_gbs[5][BREV_MAX_LOG2N + 1];
 
 int tuned_batched_b(int k, int E) {
@@ -306,6 +308,11 @@ int tuned_batched_b(int k, int E) {
 int tuned_batched_stages(int k, int E) {
   if (k < 0 || k > BREV_MAX_LOG2N || !valid_E(E)) return 0;
   return (int)g_tuned_batched_stages[e_index(E)][k].load(std::memory_order_relaxed);
+}
+
+int tuned_batched_warps(int k, int E) {
+  if (k < 0 || k > BREV_MAX_LOG2N || !valid_E(E)) return 0;
+  return (int)g_tuned_batched_warps[e_index(E)][k].load(std::memory_order_relaxed);
 }
 
 int tuned_batched_copy(int k, int E) {
@@ -683,6 +690,8 @@ void brev_reset_tuning(void) {
     for (auto& v : row) v.store(0, std::memory_order_relaxed);
   for (auto& row : g_tuned_batched_copy)
     for (auto& v : row) v.store(0, std::memory_order_relaxed);
+  for (auto& row : g_tuned_batched_warps)
+    for (auto& v : row) v.store(0, std::memory_order_relaxed);
   memset(g_tuned_batched_gbs, 0, sizeof(g_tuned_batched_gbs));
 }
 
@@ -725,10 +734,12 @@ static brev_status write_cache(const char* path) {
       if (v <= 0) continue;
       fprintf(f,
               "%s\n  {\"elem_bytes\": %d, \"log2n\": %d, \"batched_b\": %d, "
-              "\"batched_stages\": %d, \"batched_copy\": %d, \"gbs\": %.1f}",
+              "\"batched_stages\": %d, \"batched_copy\": %d, \"batched_warps\": %d, "
+              "\"gbs\": %.1f}",
               first ? "" : ",", Es[ei], k, v - 1,
               (int)g_tuned_batched_stages[ei][k].load(std::memory_order_relaxed),
               (int)g_tuned_batched_copy[ei][k].load(std::memory_order_relaxed) - 1,
+              (int)g_tuned_batched_warps[ei][k].load(std::memory_order_relaxed),
               g_tuned_batched_gbs[ei][k]);
       first = false;
     }
@@ -808,6 +819,10 @@ brev_status brev_load_tune_cache(const char* path) {
           if (bb > 0 && json_int(p, q, "batched_copy", &cp) && (cp == 0 || cp == 1))
             g_tuned_batched_copy[e_index((int)E)][k].store((int8_t)(cp + 1),
                                                            std::memory_order_relaxed);
+          long nw = 0;
+          if (json_int(p, q, "batched_warps", &nw) && (nw == 4 || nw == 8))
+            g_tuned_batched_warps[e_index((int)E)][k].store((int8_t)nw,
+                                                            std::memory_order_relaxed);
           ++loaded;
         }
       }
@@ -869,21 +884,29 @@ static brev_status autotune_batched(int k_min, int k_max, int E, cudaStream_t st
     items.assign(count, BatchItem{});
     for (int i = 0; i < count; ++i) items[i] = BatchItem{(char*)buf + (uint64_t)i * bytes, k, E};
     double best = 1e30, def_ms = 0;
-    int best_b = -1, best_s = 0, best_c = -1;
+    int best_b = -1, best_s = 0, best_c = -1, best_w = 0;
     for (int c = 0; c < nc && result == BREV_OK; ++c) {
       int sc[8];
       const int ns = batched_stage_candidates(k, E, cand[c], sc);
-      // (stages, copy) candidates: the built-in choice (0, -1) first, then
-      // every stage count with either staging (whole arrays: bulk only)
+      // (warps, stages, copy) candidates: the built-in choice (0, 0, -1)
+      // first, then both CTA shapes with every stage count and either
+      // staging (whole arrays: bulk only)
       const int ncopy = cand[c] > 0 ? 2 : 1;
-      for (int si = -1; si < ns * ncopy && result == BREV_OK; ++si) {
-        const int stages = si < 0 ? 0 : sc[si / ncopy];
-        const int copy = si < 0 ? -1 : (cand[c] > 0 ? si % ncopy : 0);
+      for (int si = -1; si < 2 * ns * ncopy && result == BREV_OK; ++si) {
+        const int warps = si < 0 ? 0 : (si / (ns * ncopy) == 0 ? 4 : 8);
+        const int rest = si < 0 ? 0 : si % (ns * ncopy);
+        const int stages = si < 0 ? 0 : sc[rest / ncopy];
+        const int copy = si < 0 ? -1 : (cand[c] > 0 ? rest % ncopy : 0);
+        BatchForce f;
+        f.b = cand[c];
+        f.stages = stages;
+        f.copy = copy;
+        f.warps = warps;
         double ms_best = 1e30;
         for (int r = 0; r < 2 + 3 && result == BREV_OK; ++r) {
           if (r >= 2) cudaEventRecord(e0, st);
           for (int j = 0; j < (r >= 2 ? R : 1) && result == BREV_OK; ++j)
-            result = batched_launch_forced(items.data(), count, cand[c], stages, copy, st);
+            result = batched_launch_forced(items.data(), count, f, st);
           if (result != BREV_OK) break;
           if (r < 2) continue;  // warm-up
           cudaEventRecord(e1, st);
@@ -898,15 +921,17 @@ static brev_status autotune_batched(int k_min, int k_max, int E, cudaStream_t st
         if (result != BREV_OK) break;
         if (tune_verbose())
           fprintf(stderr,
-                  "brev tune batched E=%d k=%d count=%d b=%d stages=%d copy=%d: %.4f ms %.1f GB/s\n",
-                  E, k, count, cand[c], stages, copy, ms_best,
+                  "brev tune batched E=%d k=%d count=%d b=%d warps=%d stages=%d copy=%d: "
+                  "%.4f ms %.1f GB/s\n",
+                  E, k, count, cand[c], warps, stages, copy, ms_best,
                   2.0 * (double)bytes * count / (ms_best * 1e-3) / 1e9);
-        if (cand[c] == def && stages == 0 && copy < 0) def_ms = ms_best;
+        if (cand[c] == def && si < 0) def_ms = ms_best;
         if (ms_best < best) {
           best = ms_best;
           best_b = cand[c];
           best_s = stages;
           best_c = copy;
+          best_w = warps;
         }
       }
     }
@@ -916,11 +941,13 @@ static brev_status autotune_batched(int k_min, int k_max, int E, cudaStream_t st
       best_b = def;
       best_s = 0;
       best_c = -1;
+      best_w = 0;
     }
     if (best_b >= 0) {
       g_tuned_batched[e_index(E)][k].store((int8_t)(best_b + 1), std::memory_order_relaxed);
       g_tuned_batched_stages[e_index(E)][k].store((int8_t)best_s, std::memory_order_relaxed);
       g_tuned_batched_copy[e_index(E)][k].store((int8_t)(best_c + 1), std::memory_order_relaxed);
+      g_tuned_batched_warps[e_index(E)][k].store((int8_t)best_w, std::memory_order_relaxed);
       g_tuned_batched_gbs[e_index(E)][k] = 2.0 * (double)bytes * count / (best * 1e-3) / 1e9;
     }
   }

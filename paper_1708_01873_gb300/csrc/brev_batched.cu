@@ -66,7 +66,7 @@ __host__ __device__ inline int batched_copy_default(int E, int b) {
 }
 
 
-constexpr int BATCH_THREADS = 256;
+constexpr int BATCH_THREADS = 256;  // consumer threads of the resident serving kernel's CTA
 #ifndef BREV_BATCHED_TICKET_BYTES
 #define BREV_BATCHED_TICKET_BYTES 262144
 #endif
@@ -264,7 +264,7 @@ __device__ __forceinline__ void issue_unit(const BatchDesc& d, unsigned u, Stage
 // Store one staged 2^b x 2^b tile (rows at pitch P, row X = rev(x), or x
 // when rev = 0) into the destination tile: output row rev(z) (or z),
 // column X.
-template <int E>
+template <int E, int NTHR>
 __device__ __forceinline__ void store_staged_tile(const unsigned char* sm, char* dst,
                                                   uint64_t stride, int b, uint32_t pitch,
                                                   int rev) {
@@ -274,7 +274,7 @@ __device__ __forceinline__ void store_staged_tile(const unsigned char* sm, char*
   const int cmask = (1 << log_c) - 1;
   const int units = 1 << (2 * log_c);
 #pragma unroll BATCH_STORE_UNROLL
-  for (int q = threadIdx.x; q < units; q += BATCH_THREADS) {
+  for (int q = threadIdx.x; q < units; q += NTHR) {
     const int cl = q & (V - 1);
     const int rest = q >> LOG_V;
     const int d = rest & cmask;
@@ -293,38 +293,49 @@ __device__ __forceinline__ void store_staged_tile(const unsigned char* sm, char*
   }
 }
 
-template <int E>
+template <int E, int NTHR>
 __device__ BREV_BATCHED_BODY_ATTR void store_staged_unit(const unsigned char* sm, char* a,
                                                         char* r, uint64_t stride, int b, int k,
                                                         int nt, int rev) {
   using C = typename ChunkT<E>::type;
   if (nt == 0) {  // small array: out[j] = in[rev j], coalesced writes
     const uint32_t n = 1u << k;
-    for (uint32_t j = threadIdx.x; j < n; j += BATCH_THREADS)
+    for (uint32_t j = threadIdx.x; j < n; j += NTHR)
       gstore<E>(a + (uint64_t)j * E,
                 *reinterpret_cast<const C*>(sm + (size_t)rev_bits(j, k) * E));
     return;
   }
   const uint32_t pitch = padded_row_bytes(E, b);
-  store_staged_tile<E>(sm, r, stride, b, pitch, rev);  // tile a's data into tile r
-  if (nt == 2) store_staged_tile<E>(sm + ((uint32_t)pitch << b), a, stride, b, pitch, rev);
+  store_staged_tile<E, NTHR>(sm, r, stride, b, pitch, rev);  // tile a's data into tile r
+  if (nt == 2) store_staged_tile<E, NTHR>(sm + ((uint32_t)pitch << b), a, stride, b, pitch, rev);
 }
 
-// Warps 0..7 store (consumers, threads 0..255); warp 8 is the producer.
-// Stage p serves units p, p + S, p + 2S, ... (S = `stages`).  full[p]
-// completes when the unit's copies have landed (one producer arrival plus
-// the bytes); empty[p] completes when all 8 consumer warps have read the
-// stage.  No block-wide barrier after the set-up: each consumer warp moves
-// on as soon as its own share of a unit is stored.
-constexpr int BATCH_CONSUMER_WARPS = BATCH_THREADS / 32;
+// CTA shape of the batched kernel: CW consumer warps (threads 0 .. 32 CW - 1)
+// and one producer warp after them.  Stage p serves units p, p + S, p + 2S,
+// ... (S = `stages`).  full[p] completes when the unit's copies have landed
+// (one producer arrival plus the bytes); empty[p] completes when all CW
+// consumer warps have read the stage.  No block-wide barrier after the
+// set-up: each consumer warp moves on as soon as its own share of a unit
+// is stored.  Two shapes are compiled: 8 consumer warps at up to 3 CTAs per
+// SM and 4 at up to 6; the launch picks one (tuned per (k, E), else 4).
+// On GB300 the 4-warp shape moved complex<float> batches from 5.9-6.3 to
+// 6.6 TB/s and float32 ones by 3 %, and matched 8 warps on complex<double>.
+constexpr int BATCH_CONSUMER_WARPS = BATCH_THREADS / 32;  // resident serving kernel
 constexpr int BATCH_BLOCK = BATCH_THREADS + 32;
+template <int CW> struct BatchShape {
+  static constexpr int THREADS = 32 * CW;       // consumer threads
+  static constexpr int BLOCK = THREADS + 32;    // + the producer warp
+  static constexpr int MIN_CTAS = CW >= 8 ? BREV_BATCHED_MIN_CTAS : 2 * BREV_BATCHED_MIN_CTAS;
+};
 
 // count > 0: descriptors desc[0..count) in global memory; count = 0: the
 // single descriptor `one`, passed by value.
-__global__ void __launch_bounds__(BATCH_BLOCK, BREV_BATCHED_MIN_CTAS)
+template <int CW>
+__global__ void __launch_bounds__(BatchShape<CW>::BLOCK, BatchShape<CW>::MIN_CTAS)
     k_batched(const BatchDesc* __restrict__ desc, int count, const BatchDesc one,
               unsigned long long tickets, unsigned long long* ticket_ctr,
               unsigned stage_bytes, int stages) {
+  constexpr int NTHR = BatchShape<CW>::THREADS;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[BATCH_MAX_STAGES], empty[BATCH_MAX_STAGES];
   __shared__ StageInfo info[BATCH_MAX_STAGES];
@@ -333,13 +344,13 @@ __global__ void __launch_bounds__(BATCH_BLOCK, BREV_BATCHED_MIN_CTAS)
   if (tid == 0) {
     for (unsigned i = 0; i < S; ++i) {
       mbar_init(&full[i], 1);
-      mbar_init(&empty[i], BATCH_CONSUMER_WARPS);
+      mbar_init(&empty[i], CW);
     }
     mbar_init_fence();
   }
   __syncthreads();  // barriers initialised
 
-  if (tid >= BATCH_THREADS) {
+  if (tid >= NTHR) {
     // ---- producer warp: tickets -> units -> bulk copies
     int a = -1;
     unsigned u = 0, ulast = 0;
@@ -410,9 +421,9 @@ __global__ void __launch_bounds__(BATCH_BLOCK, BREV_BATCHED_MIN_CTAS)
     if (s.nt < 0) return;
     const unsigned char* buf = smem + (size_t)st * stage_bytes;
     switch (s.E) {
-      case 16: store_staged_unit<16>(buf, s.a, s.r, s.stride, s.b, s.k, s.nt, s.rev); break;
-      case 8: store_staged_unit<8>(buf, s.a, s.r, s.stride, s.b, s.k, s.nt, s.rev); break;
-      case 4: store_staged_unit<4>(buf, s.a, s.r, s.stride, s.b, s.k, s.nt, s.rev); break;
+      case 16: store_staged_unit<16, NTHR>(buf, s.a, s.r, s.stride, s.b, s.k, s.nt, s.rev); break;
+      case 8: store_staged_unit<8, NTHR>(buf, s.a, s.r, s.stride, s.b, s.k, s.nt, s.rev); break;
+      case 4: store_staged_unit<4, NTHR>(buf, s.a, s.r, s.stride, s.b, s.k, s.nt, s.rev); break;
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[st]);
@@ -688,9 +699,15 @@ __global__ void __launch_bounds__(SERVE_BLOCK, BREV_BATCHED_MIN_CTAS)
     if (s.nt < 0) return;
     const unsigned char* buf = smem + (size_t)st * A.stage_bytes;
     switch (s.E) {
-      case 16: store_staged_unit<16>(buf, s.a, s.r, s.stride, s.b, s.k, s.nt, s.rev); break;
-      case 8: store_staged_unit<8>(buf, s.a, s.r, s.stride, s.b, s.k, s.nt, s.rev); break;
-      case 4: store_staged_unit<4>(buf, s.a, s.r, s.stride, s.b, s.k, s.nt, s.rev); break;
+      case 16:
+        store_staged_unit<16, BATCH_THREADS>(buf, s.a, s.r, s.stride, s.b, s.k, s.nt, s.rev);
+        break;
+      case 8:
+        store_staged_unit<8, BATCH_THREADS>(buf, s.a, s.r, s.stride, s.b, s.k, s.nt, s.rev);
+        break;
+      case 4:
+        store_staged_unit<4, BATCH_THREADS>(buf, s.a, s.r, s.stride, s.b, s.k, s.nt, s.rev);
+        break;
     }
     // Completion accounting, one global atomic per ticket and CTA: each
     // warp counts itself on the stage's shared counter (a release at CTA
@@ -792,7 +809,7 @@ static void batched_smem_limits(int* per_sm, int* per_block, int* static_bytes) 
             cudaSuccess ||
         cudaDeviceGetAttribute(&blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
             cudaSuccess ||
-        cudaFuncGetAttributes(&fa, (const void*)k_batched) != cudaSuccess) {
+        cudaFuncGetAttributes(&fa, (const void*)k_batched<8>) != cudaSuccess) {
       cudaGetLastError();
       sm = 228 * 1024;
       blk = 227 * 1024;
@@ -814,16 +831,27 @@ static int batched_stages_cap(unsigned stage_bytes) {
   return std::max(2, std::min(BATCH_MAX_STAGES, cap));
 }
 
-// Built-in stage count: as many stages as fit while BREV_BATCHED_MIN_CTAS
-// CTAs share one SM's shared memory (each CTA also holds its static shared
-// memory and the 1 KiB the hardware reserves per CTA), 2 .. BATCH_MAX_STAGES.
-// More stages keep more bytes in flight per CTA: one 16 KiB tile pair of
-// 8-byte elements per CTA left the kernel latency-bound (5.2 TB/s on equal
-// arrays), two 32 KiB pairs do not.
-static int batched_stages_default(unsigned stage_bytes) {
+// CTA shapes of the batched kernel (consumer warps) and their properties.
+constexpr int BATCH_WARPS_DEFAULT = 4;
+static bool batched_warps_ok(int cw) { return cw == 4 || cw == 8; }
+static const void* batched_kernel(int cw) {
+  return cw == 8 ? (const void*)k_batched<8> : (const void*)k_batched<4>;
+}
+static int batched_block(int cw) { return cw == 8 ? BatchShape<8>::BLOCK : BatchShape<4>::BLOCK; }
+static int batched_min_ctas(int cw) {
+  return cw == 8 ? BatchShape<8>::MIN_CTAS : BatchShape<4>::MIN_CTAS;
+}
+
+// Built-in stage count: as many stages as fit while the shape's intended
+// CTAs per SM share one SM's shared memory (each CTA also holds its static
+// shared memory and the 1 KiB the hardware reserves per CTA),
+// 2 .. BATCH_MAX_STAGES.  More stages keep more bytes in flight per CTA:
+// one 16 KiB tile pair of 8-byte elements per CTA left the 8-warp kernel
+// latency-bound (5.2 TB/s on equal arrays), two 32 KiB pairs do not.
+static int batched_stages_default(unsigned stage_bytes, int cw) {
   int sm, blk, st;
   batched_smem_limits(&sm, &blk, &st);
-  const int budget = sm / BREV_BATCHED_MIN_CTAS - 1024 - st;
+  const int budget = sm / batched_min_ctas(cw) - 1024 - st;
   const int s = stage_bytes ? budget / (int)stage_bytes : BATCH_MAX_STAGES;
   return std::max(2, std::min(batched_stages_cap(stage_bytes), s));
 }
@@ -836,10 +864,10 @@ int batched_stage_candidates(int k, int E, int b, int* out) {
   return n;
 }
 
-static int batched_grid(unsigned smem) {
+static int batched_grid(unsigned smem, int cw) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched, BATCH_BLOCK, smem) !=
-          cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel(cw), batched_block(cw),
+                                                    smem) != cudaSuccess ||
       per_sm < 1) {
     cudaGetLastError();
     per_sm = 1;
@@ -852,6 +880,7 @@ struct BatchPlanData {
   unsigned long long tickets = 0;
   unsigned stage_bytes = 0;  // shared memory of one pipeline stage
   int stages = 0;            // pipeline stages per CTA
+  int warps = 0;             // consumer warps per CTA (the CTA shape)
   std::vector<BatchItem> fallback;  // arrays run with single-array launches
 };
 
@@ -863,11 +892,12 @@ constexpr unsigned long long BATCH_GUIDE = 4;
 // Descriptors beyond one per array that the guided split may add.
 constexpr int BATCH_EXTRA_DESC = 24;
 
-// Descriptors and tickets of a batch; force_b >= 0 imposes that tile
-// exponent on every array (which must accept it), force_stages > 0 the
-// stage count.
+// Descriptors and tickets of a batch; f.b >= 0 imposes that tile exponent
+// on every array (which must accept it), f.stages > 0 the stage count,
+// f.copy >= 0 the row staging and f.warps > 0 the CTA shape.
 static brev_status build_batch(const BatchItem* items, int count, BatchPlanData* out,
-                               int force_b = -1, int force_stages = 0, int force_copy = -1) {
+                               const BatchForce& f = BatchForce{}) {
+  const int force_b = f.b, force_stages = f.stages, force_copy = f.copy;
   struct Tmp {
     BatchDesc d;
     unsigned long long bytes, unit_bytes;
@@ -906,12 +936,14 @@ static brev_status build_batch(const BatchItem* items, int count, BatchPlanData*
       unit_bytes = 2ull * ((unsigned long long)it.E << (2 * b));
     }
     const unsigned stage = stage_unit_bytes(it.k, it.E, b);
-    // the array with the largest stage sets the stage count (tuned per
-    // (k, E), else as many as fit)
+    // the array with the largest stage sets the CTA shape and the stage
+    // count (tuned per (k, E), else the built-in ones)
     if (stage > out->stage_bytes) {
       out->stage_bytes = stage;
       const int ts = tuned_batched_stages(it.k, it.E);
       out->stages = ts > 0 ? ts : 0;
+      const int tw = tuned_batched_warps(it.k, it.E);
+      out->warps = batched_warps_ok(tw) ? tw : 0;
     }
     // about BATCH_TICKET_BYTES of tile data per ticket
     const unsigned long long g =
@@ -919,8 +951,10 @@ static brev_status build_batch(const BatchItem* items, int count, BatchPlanData*
     d.grain = (unsigned)std::min<unsigned long long>(g, d.units);
     tmp.push_back({d, (unsigned long long)it.E << it.k, unit_bytes, stage});
   }
+  if (f.warps > 0) out->warps = f.warps;
+  if (!batched_warps_ok(out->warps)) out->warps = BATCH_WARPS_DEFAULT;
   if (force_stages > 0) out->stages = force_stages;
-  if (out->stages <= 0) out->stages = batched_stages_default(out->stage_bytes);
+  if (out->stages <= 0) out->stages = batched_stages_default(out->stage_bytes, out->warps);
   out->stages = std::min(out->stages, batched_stages_cap(out->stage_bytes));
   // largest arrays first: the long-running tickets start early and the
   // small ones fill the tail
@@ -930,7 +964,8 @@ static brev_status build_batch(const BatchItem* items, int count, BatchPlanData*
   // x the ticket's bytes, keep the grain; below, halve it (down to one
   // unit), splitting an array across descriptors where its grain changes
   const unsigned long long P =
-      tmp.empty() ? 1 : (unsigned long long)batched_grid(out->stages * out->stage_bytes);
+      tmp.empty() ? 1
+                  : (unsigned long long)batched_grid(out->stages * out->stage_bytes, out->warps);
   unsigned long long left = 0;
   for (const auto& x : tmp) left += x.unit_bytes * x.d.units;
   unsigned long long t = 0;
@@ -969,28 +1004,32 @@ static brev_status build_batch(const BatchItem* items, int count, BatchPlanData*
 }
 
 // Launch the persistent kernel over `count` descriptors already on the
-// device (ticket counter zeroed in stream order before it), with `stages`
-// pipeline stages (0: the built-in count for the stage size).
+// device (ticket counter zeroed in stream order before it), with `warps`
+// consumer warps per CTA (0: the built-in shape) and `stages` pipeline
+// stages (0: the built-in count for the shape and stage size).
 static brev_status launch_batched_kernel(const BatchDesc* d_desc, int count,
                                          unsigned long long tickets,
                                          unsigned long long* d_ticket, unsigned stage_bytes,
-                                         int stages, cudaStream_t stream,
+                                         int stages, int warps, cudaStream_t stream,
                                          const BatchDesc* one = nullptr) {
   BatchDesc one_v{};
   if (one) one_v = *one;
-  if (stages <= 0) stages = batched_stages_default(stage_bytes);
+  if (warps <= 0) warps = BATCH_WARPS_DEFAULT;
+  if (!batched_warps_ok(warps))
+    return set_error(BREV_ERR_INVALID_ARG, "%d consumer warps per CTA", warps);
+  if (stages <= 0) stages = batched_stages_default(stage_bytes, warps);
   if (stages < 2 || stages > BATCH_MAX_STAGES || stages > batched_stages_cap(stage_bytes))
     return set_error(BREV_ERR_INVALID_ARG, "stage count %d for stages of %u bytes", stages,
                      stage_bytes);
   const unsigned smem = (unsigned)stages * stage_bytes;
-  cudaError_t e = ensure_smem((const void*)k_batched, smem);
+  const void* kern = batched_kernel(warps);
+  cudaError_t e = ensure_smem(kern, smem);
   if (e != cudaSuccess) return cuda_error(e, "shared-memory limit of the batched kernel");
   const int grid =
-      (int)std::min<unsigned long long>((unsigned long long)batched_grid(smem), tickets);
+      (int)std::min<unsigned long long>((unsigned long long)batched_grid(smem, warps), tickets);
   void* args[] = {(void*)&d_desc, (void*)&count, (void*)&one_v, (void*)&tickets,
                   (void*)&d_ticket, (void*)&stage_bytes, (void*)&stages};
-  e = cudaLaunchKernel((const void*)k_batched, dim3(grid), dim3(BATCH_BLOCK), args, smem,
-                       stream);
+  e = cudaLaunchKernel(kern, dim3(grid), dim3(batched_block(warps)), args, smem, stream);
   if (e != cudaSuccess) return cuda_error(e, "batched kernel launch");
   note_launch();
   return BREV_OK;
@@ -1004,7 +1043,7 @@ static brev_status enqueue_batch(const BatchPlanData& p, const BatchDesc* d_desc
     cudaError_t e = cudaMemsetAsync(d_ticket, 0, sizeof(unsigned long long), stream);
     if (e != cudaSuccess) return cuda_error(e, "ticket reset");
     brev_status s = launch_batched_kernel(d_desc, (int)p.desc.size(), p.tickets, d_ticket,
-                                          p.stage_bytes, p.stages, stream);
+                                          p.stage_bytes, p.stages, p.warps, stream);
     if (s != BREV_OK) return s;
   }
   for (const BatchItem& it : p.fallback) {
@@ -1016,17 +1055,18 @@ static brev_status enqueue_batch(const BatchPlanData& p, const BatchDesc* d_desc
 
 void preload_batched() {
   cudaFuncAttributes fa;
-  if (cudaFuncGetAttributes(&fa, (const void*)k_batched) != cudaSuccess) cudaGetLastError();
+  for (int cw : {4, 8})
+    if (cudaFuncGetAttributes(&fa, batched_kernel(cw)) != cudaSuccess) cudaGetLastError();
 }
 
 brev_status batched_launch(const BatchItem* items, int count, cudaStream_t stream) {
-  return batched_launch_forced(items, count, -1, 0, -1, stream);
+  return batched_launch_forced(items, count, BatchForce{}, stream);
 }
 
-brev_status batched_launch_forced(const BatchItem* items, int count, int b, int stages, int copy,
+brev_status batched_launch_forced(const BatchItem* items, int count, const BatchForce& f,
                                   cudaStream_t stream) {
   BatchPlanData p;
-  brev_status s = build_batch(items, count, &p, b, stages, copy);
+  brev_status s = build_batch(items, count, &p, f);
   if (s != BREV_OK) return s;
   if (p.desc.empty()) return enqueue_batch(p, nullptr, nullptr, stream);
   // stream-ordered workspace: descriptors + ticket counter
@@ -1079,8 +1119,9 @@ brev_status bitrev_inplace_pipelined(void* data, int k, int E, int b, cudaStream
   d.units = (unsigned)units;
   // about 8 tickets per resident CTA (the tail of the last wave stays short)
   const unsigned stage = stage_unit_bytes(k, E, b);
-  const int stages = batched_stages_default(stage);
-  const unsigned long long ctas = (unsigned long long)batched_grid(stages * stage);
+  const int stages = batched_stages_default(stage, BATCH_WARPS_DEFAULT);
+  const unsigned long long ctas =
+      (unsigned long long)batched_grid(stages * stage, BATCH_WARPS_DEFAULT);
   const unsigned long long unit_bytes = 2ull * ((unsigned long long)E << (2 * b));
   d.grain = (unsigned)std::min<unsigned long long>(
       std::max<unsigned long long>(1, units / (8 * ctas)),
@@ -1100,7 +1141,7 @@ brev_status bitrev_inplace_pipelined(void* data, int k, int E, int b, cudaStream
     return cuda_error(e, "ticket reset");
   }
   brev_status st =
-      launch_batched_kernel(nullptr, 0, tickets, d_ticket, stage, stages, stream, &d);
+      launch_batched_kernel(nullptr, 0, tickets, d_ticket, stage, stages, 0, stream, &d);
   ws_free(ws, stream);
   return st;
 }
@@ -1171,7 +1212,7 @@ brev_status transpose_inplace_pipelined(void* data, int a, int E, cudaStream_t s
     return cuda_error(e, "ticket reset");
   }
   brev_status st = launch_batched_kernel(nullptr, 0, tickets, d_ticket,
-                                         stage_unit_bytes(2 * b, E, b), 0, stream, &d);
+                                         stage_unit_bytes(2 * b, E, b), 0, 0, stream, &d);
   ws_free(ws, stream);
   return st;
 }
@@ -1577,7 +1618,7 @@ extern "C" brev_status brev_permute_batched_noalloc(void* const* ptr_array,
     if (e != cudaSuccess) return cuda_error(e, "descriptor upload (no-alloc)");
     e = cudaMemsetAsync(d_ticket, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return cuda_error(e, "ticket reset (no-alloc)");
-    s = launch_batched_kernel(d_desc, nd, tickets, d_ticket, stage_bytes, 0, st);
+    s = launch_batched_kernel(d_desc, nd, tickets, d_ticket, stage_bytes, 0, 0, st);
     if (s != BREV_OK) return s;
   }
   for (int i = 0; i < nf; ++i) {

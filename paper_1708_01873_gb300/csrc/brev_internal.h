@@ -75,12 +75,18 @@ brev_status batched_launch(const BatchItem* items, int count, cudaStream_t strea
 size_t batched_ws_bytes(int count);
 brev_status batched_launch_into(const BatchItem* items, int count, void* ws, size_t ws_bytes,
                                 cudaStream_t stream);
-// The same launch with tile exponent `b` forced for every array (b < 0:
-// the usual choice; each array must accept b, see batched_candidates) and
-// `stages` pipeline stages (0: the usual choice) and tile rows staged as
-// `copy` (0: bulk copies, 1: per-thread chunks, -1: the usual choice) --
-// the tuner's candidates.
-brev_status batched_launch_forced(const BatchItem* items, int count, int b, int stages, int copy,
+// Choices of a batched launch imposed on it (the tuner's candidates): tile
+// exponent b for every array (-1: the usual choice; each array must accept
+// b, see batched_candidates), pipeline stages (0: usual), tile rows staged
+// as bulk copies (0) or per-thread chunks (1) (-1: usual), and consumer
+// warps per CTA, 4 or 8 (0: usual).
+struct BatchForce {
+  int b = -1;
+  int stages = 0;
+  int copy = -1;
+  int warps = 0;
+};
+brev_status batched_launch_forced(const BatchItem* items, int count, const BatchForce& f,
                                   cudaStream_t stream);
 // Stage counts the batched kernel can run with stages of the array (k, E)
 // at tile exponent b, into out[0..return).
@@ -143,6 +149,9 @@ brev_status bitrev_inplace_pipelined(void* data, int k, int E, int b, cudaStream
 // a batch whose largest stage is this array's, or 0 (brev_api.cu).
 int tuned_batched_b(int k, int E);
 int tuned_batched_stages(int k, int E);
+// Tuned consumer warps per CTA of a batch whose largest stage is an array
+// (k, E), or 0.
+int tuned_batched_warps(int k, int E);
 // Tuned staging of the array's tile rows (0 bulk, 1 chunks), or -1.
 int tuned_batched_copy(int k, int E);
 // Argument checks of a batch (sizes, alignment, device ranges, no overlap).

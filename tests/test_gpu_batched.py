@@ -267,7 +267,8 @@ def _cache_for(brev_lib, entries):
 
 @pytest.mark.parametrize("E,b", [(4, 5), (4, 6), (8, 4), (8, 5), (16, 3), (16, 4), (16, 5)])
 def test_batched_every_stage_count_and_staging(brev_lib, oracle_lib, cuda_device, tmp_path, E, b):
-    """Every (tile exponent, stage count, row staging) the tuner may pick,
+    """Every (tile exponent, CTA shape, stage count, row staging) the tuner
+    may pick,
     imposed through a tuning cache on arrays of k = 2b + 3 (several tile
     pairs and self tiles each), batched with smaller arrays of the same
     element size whose stages are smaller, so that the launch takes the
@@ -280,30 +281,30 @@ def test_batched_every_stage_count_and_staging(brev_lib, oracle_lib, cuda_device
     # stage counts that fit one CTA for this array's stage (2 .. 6)
     path = str(tmp_path / "t.json")
     tried = 0
-    for stages in range(2, 7):
-        for copy in (0, 1):
-            with open(path, "w") as f:
-                f.write(_cache_for(brev_lib, [{"elem_bytes": E, "log2n": k, "batched_b": b,
-                                               "batched_stages": stages, "batched_copy": copy,
-                                               "gbs": 1.0}]))
-            brev_lib.brev_reset_tuning()
-            brev_lib.brev_load_tune_cache(path)
-            if brev_lib.brev_batched_shape(k, E) != b:
-                continue  # not a candidate for this (k, E)
-            rng = np.random.default_rng(1000 * E + 10 * stages + copy)
-            arrays, hosts = _make_batch(rng, 96, [k], [E], 5000 + 100 * stages + copy)
-            # smaller arrays ride along under the same stage count (their stages are
-            # smaller: a smaller tile, or the whole array staged)
-            more, more_h = _make_batch(rng, 40, list(range(2, 2 * b)), [E], 7000 + stages)
-            t0 = brev_lib.brev_wait_timeouts()
-            brev_lib.brev_permute_batched(arrays + more)
-            torch.cuda.synchronize()
-            assert brev_lib.brev_wait_timeouts() == t0
-            for a, ex, (kk, EE, _) in zip(arrays + more, _expect(oracle_lib, hosts + more_h),
-                                          hosts + more_h):
-                assert_bytes_equal(to_bytes(a), ex, EE,
-                                   f"E={E} b={b} stages={stages} copy={copy} k={kk} E'={EE}")
-            tried += 1
-    assert tried >= 2
+    for warps, stages, copy in [(w, s_, c) for w in (4, 8) for s_ in range(2, 7) for c in (0, 1)]:
+        with open(path, "w") as f:
+            f.write(_cache_for(brev_lib, [{"elem_bytes": E, "log2n": k, "batched_b": b,
+                                           "batched_stages": stages, "batched_copy": copy,
+                                           "batched_warps": warps, "gbs": 1.0}]))
+        brev_lib.brev_reset_tuning()
+        brev_lib.brev_load_tune_cache(path)
+        if brev_lib.brev_batched_shape(k, E) != b:
+            continue  # not a candidate for this (k, E)
+        rng = np.random.default_rng(1000 * E + 100 * warps + 10 * stages + copy)
+        arrays, hosts = _make_batch(rng, 96, [k], [E], 5000 + 100 * stages + copy + warps)
+        # smaller arrays ride along under the same stage count (their stages are
+        # smaller: a smaller tile, or the whole array staged)
+        more, more_h = _make_batch(rng, 40, list(range(2, 2 * b)), [E], 7000 + stages)
+        t0 = brev_lib.brev_wait_timeouts()
+        brev_lib.brev_permute_batched(arrays + more)
+        torch.cuda.synchronize()
+        assert brev_lib.brev_wait_timeouts() == t0
+        for a, ex, (kk, EE, _) in zip(arrays + more, _expect(oracle_lib, hosts + more_h),
+                                      hosts + more_h):
+            assert_bytes_equal(to_bytes(a), ex, EE,
+                               f"E={E} b={b} warps={warps} stages={stages} copy={copy} "
+                               f"k={kk} E'={EE}")
+        tried += 1
+    assert tried >= 4
     brev_lib.brev_reset_tuning()
     brev_lib.brev_load_tune_cache(brev_lib.DEFAULT_TUNE_CACHE)  # the state later tests expect

@@ -396,11 +396,13 @@ BATCHED_SHAPES = {16: (3, 4, 5), 8: (4, 5), 4: (5, 6)}
 BATCHED_BMIN = {16: 3, 8: 4, 4: 5}
 
 
+@pytest.mark.parametrize("nthr", (128, 256))
 @pytest.mark.parametrize("copy", (0, 1))
 @pytest.mark.parametrize("E", sorted(BATCHED_SHAPES))
-def test_batched_staged_index_math(E, copy):
-    """TMA-staged batched kernel, tile rows staged as bulk copies (copy 0)
-    or as per-thread 16-byte chunks (copy 1): copies in bounds, 16-byte
+def test_batched_staged_index_math(E, copy, nthr):
+    """TMA-staged batched kernel with 4 or 8 consumer warps (nthr), tile
+    rows staged as bulk copies (copy 0) or as per-thread 16-byte chunks
+    (copy 1): copies in bounds, 16-byte
     aligned and counted in the expected bytes; every staged chunk read once
     per tile without bank conflicts; every element moved once to rev(i)."""
     cases = [(k, 0) for k in range(2, 16)
@@ -411,7 +413,7 @@ def test_batched_staged_index_math(E, copy):
         units = 1 if b == 0 else count_lt(k - 2 * b) + count_self(k - 2 * b)
         loads, stores, conf = [], [], 0
         for u in range(units):
-            lo, st, c = emulate_staged_unit(E, b, k, u, copy=copy)
+            lo, st, c = emulate_staged_unit(E, b, k, u, nthr=nthr, copy=copy)
             loads += lo
             stores += st
             conf += c
@@ -423,7 +425,7 @@ def test_batched_staged_index_math(E, copy):
         T = 1 << (a - b)
         loads, stores, conf = [], [], 0
         for u in range(T * (T - 1) // 2 + T):
-            lo, st, c = emulate_staged_unit(E, b, a, u, transpose=True, copy=copy)
+            lo, st, c = emulate_staged_unit(E, b, a, u, nthr=nthr, transpose=True, copy=copy)
             loads += lo
             stores += st
             conf += c
