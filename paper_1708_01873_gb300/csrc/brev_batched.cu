@@ -490,6 +490,17 @@ constexpr int SERVE_BLOCK = BATCH_BLOCK + 32;  // consumers, producer, dispatche
 #ifndef BREV_SERVE_MAX_TICKET_BYTES
 #define BREV_SERVE_MAX_TICKET_BYTES 65536
 #endif
+// Tickets of requests admitted while at least BREV_SERVE_BACKLOG_REQUESTS
+// requests are in flight: queueing then sets their latency, and larger
+// tickets (fewer claims and descriptor lookups per byte) raise the
+// throughput the backlog drains at.  (Counting outstanding tickets instead
+// switched on behind every single 512 MB request and coarsened its tail.)
+#ifndef BREV_SERVE_BACKLOG_TICKET_BYTES
+#define BREV_SERVE_BACKLOG_TICKET_BYTES 262144
+#endif
+#ifndef BREV_SERVE_BACKLOG_REQUESTS
+#define BREV_SERVE_BACKLOG_REQUESTS 16
+#endif
 
 
 // Dispatcher warp: host ring -> device ring and ticket table.
@@ -1221,7 +1232,8 @@ brev_status transpose_inplace_pipelined(void* data, int a, int E, cudaStream_t s
 // A request's units are spread over about two tickets per resident CTA (a
 // request finishes soonest when all CTAs share it), with tickets of one
 // unit at least and of about 256 KiB at most.
-bool resident_shape(int k, int E, int ctas, int* b, unsigned* units, unsigned* grain) {
+bool resident_shape(int k, int E, int ctas, bool backlog, int* b, unsigned* units,
+                    unsigned* grain) {
   if (!(E == 4 || E == 8 || E == 16) || k <= 1 || k > BREV_MAX_LOG2N) return false;
   const int bb = batched_b(k, E);
   if (bb < 0) return false;
@@ -1237,6 +1249,11 @@ bool resident_shape(int k, int E, int ctas, int* b, unsigned* units, unsigned* g
   if (n_units > 0x7FFFFFFFull) return false;
   *b = bb;
   *units = (unsigned)n_units;
+  if (backlog) {  // the CTAs have work queued: large tickets, fewer claims per byte
+    *grain = (unsigned)std::min<unsigned long long>(
+        n_units, std::max<unsigned long long>(1, BREV_SERVE_BACKLOG_TICKET_BYTES / unit_bytes));
+    return true;
+  }
   const unsigned long long max_grain =
       std::max<unsigned long long>(1, BREV_SERVE_MAX_TICKET_BYTES / unit_bytes);
   *grain = (unsigned)std::min<unsigned long long>(
@@ -1246,6 +1263,8 @@ bool resident_shape(int k, int E, int ctas, int* b, unsigned* units, unsigned* g
       max_grain);
   return true;
 }
+
+int resident_backlog_requests() { return BREV_SERVE_BACKLOG_REQUESTS; }
 
 // Stage size that holds any unit the resident kernel may meet (every
 // (E, b) the batched path accepts, and whole arrays of up to 32 KiB).

@@ -139,7 +139,12 @@ void resident_free(ResidentState* st);
 brev_status resident_launch(ResidentState* st, cudaStream_t stream, unsigned long long idle_ns);
 // Units, grain and tile exponent of a request in the resident kernel;
 // false if it cannot run there (elem sizes 1, 2; k <= 1).
-bool resident_shape(int k, int E, int ctas, int* b, unsigned* units, unsigned* grain);
+// backlog: many requests are already in flight (larger tickets then).
+bool resident_shape(int k, int E, int ctas, bool backlog, int* b, unsigned* units,
+                    unsigned* grain);
+// Requests in flight from which new ones are admitted with backlog-sized
+// tickets.
+int resident_backlog_requests();
 // Single arrays on the pipeline (launch order 2): valid tile exponents,
 // the list of them for E, and the launch.
 bool pipeline_shape_ok(int k, int E, int b);

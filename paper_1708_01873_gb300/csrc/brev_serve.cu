@@ -286,7 +286,9 @@ brev_status run_resident(brev_server* srv, std::vector<Req>& reqs, int hold_resu
       Req& r = reqs[waiting.front()];
       int b = 0;
       unsigned units = 0, grain = 1;
-      if (!resident_shape(r.k, r.E, R.ctas, &b, &units, &grain)) {
+      // many requests in flight at once: the server is queueing
+      const bool backlog = (int)live.size() >= resident_backlog_requests();
+      if (!resident_shape(r.k, r.E, R.ctas, backlog, &b, &units, &grain)) {
         result = set_error(BREV_ERR_UNSUPPORTED, "request k=%d E=%d in resident mode", r.k, r.E);
         break;
       }
