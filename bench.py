@@ -407,11 +407,14 @@ def run_brev(args):
             torch, brev, inputs, device, stream, sampler, reduce_max, barrier, peak,
             k=args.next_k))
 
-    # -------------------------- one array over all ranks (N > 1 only)
+    # ---------- one array over all ranks (N > 1), or its local passes (N = 1)
     distributed = None
     if ws > 1:
         distributed = section("distributed", lambda: bench_distributed(
             torch, brev, device, stream, sampler, reduce_max, barrier, ws, rank))
+    elif not args.no_next:
+        distributed = section("distributed local passes", lambda: bench_dist_local(
+            torch, brev, device, stream, sampler, barrier, peak))
 
     # ------------------------------------------------------------ e2e
     e2e = None
@@ -745,6 +748,37 @@ def bench_distributed(torch, brev, device, stream, sampler, reduce_max, barrier,
             "rank0_pack_ms": round(pack, 4), "rank0_all_to_all_ms": round(a2a, 4),
             "rank0_finish_ms": round(fin, 4),
             "exchange": "torch.distributed.all_to_all_single (NCCL), equal segments"}
+
+
+def bench_dist_local(torch, brev, device, stream, sampler, barrier, peak, log2_block=27,
+                     reps=5, warm=2):
+    """One GPU: the two local passes of the permutation spread over G = 2, 4,
+    8, 16 ranks, on one rank's block of 2^27 complex<double> (2 GiB) --
+    the pack (a (k-g)-bit permutation in place) and the finish (a 2^g x
+    2^(k-2g) transposition with bit-reversed rows, out of place) -- each
+    timed back to back with CUDA events.  The exchange between them needs
+    several GPUs and is not run here."""
+    E = 16
+    blk = torch.empty((1 << log2_block) * E, dtype=torch.uint8, device=device)
+    blk.fill_(0x3C)
+    rcv = torch.empty_like(blk)
+    b = blk.view(torch.complex128)
+    r = rcv.view(torch.complex128)
+    nbytes = 2 * blk.numel()
+    timed = event_timer(torch, stream, sampler, lambda x: x, barrier, reps, warm)
+    out = {"block": f"2^{log2_block} complex<double> (2 GiB) per rank"}
+    for g in (1, 2, 3, 4):
+        k = log2_block + g
+        pack = timed(lambda: brev.brev_dist_pack(b, b, k, g, stream))
+        fin = timed(lambda: brev.brev_dist_finish(b, r, k, g, stream))
+        out[f"G{1 << g}"] = {"pack_ms": round(pack, 4),
+                             "pack_gbs": round(nbytes / (pack * 1e-3) / 1e9, 1),
+                             "finish_ms": round(fin, 4),
+                             "finish_gbs": round(nbytes / (fin * 1e-3) / 1e9, 1),
+                             "finish_frac": round(nbytes / (fin * 1e-3) / 1e9 / peak, 4)}
+    del blk, rcv
+    torch.cuda.empty_cache()
+    return out
 
 
 def bench_next(torch, brev, inputs, device, stream, sampler, reduce_max, barrier, peak,

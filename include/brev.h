@@ -285,7 +285,8 @@ BREV_API brev_status brev_fft_stages(void *dst, const void *src, int log2n, int 
  *   - admission is the same (FIFO head, slots, pool), plus room in the ring
  *     (4096 requests) and in the kernel's ticket window (2^22 tickets);
  *   - each admitted request is written into the ring and published at once;
- *     the kernel spreads its tile units over all CTAs (~64 KiB tickets), so
+ *     the kernel spreads its tile units over all CTAs (~64 KiB tickets, or
+ *     256 KiB while 16 or more requests are in flight), so
  *     requests in flight overlap on the device;
  *   - the kernel writes a completion word per request into host memory;
  *   - element sizes 4, 8 and 16 only (BREV_ERR_UNSUPPORTED otherwise);
