@@ -143,6 +143,34 @@ def test_resident_server_results_equal_alone(brev_lib, oracle_lib, cuda_device):
     assert brev_lib.brev_wait_timeouts() == t0
 
 
+def test_resident_server_backlog_results_equal_alone(brev_lib, cuda_device):
+    """Resident mode above the device's bandwidth (about 8 TB/s offered in
+    requests of 2 to 64 MiB): the backlog reaches 16 requests in flight, so
+    requests are admitted with the large backlog tickets.  Every request's
+    region equals the single-array permutation of its initial bytes
+    (compared on the device)."""
+    t0 = brev_lib.brev_wait_timeouts()
+    arena = torch.empty(16 << 30, dtype=torch.uint8, device="cuda")
+    inputs.fill_torch(arena, 97, "u8", chunk=1 << 28)
+    initial = arena.clone()
+    torch.cuda.synchronize()
+    stats, trace = brev_lib.brev_server_run_poisson(
+        arena, seed=13, rate_per_s=300000.0, seconds=0.0015, k_range=(19, 22),
+        elem_sizes=(4, 8, 16), max_slots=64, hold_results=True, trace=True, resident=True)
+    torch.cuda.synchronize()
+    assert stats["completed"] == stats["offered"] == len(trace) > 250
+    assert stats["max_inflight"] >= 16   # the backlog tickets were in use
+    for i, r in enumerate(trace):
+        E, k, off = r["elem_bytes"], r["log2n"], r["offset"]
+        nb = E << k
+        alone = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        brev_lib.brev_permute_to(alone.view(DTYPE[E]), initial[off:off + nb].view(DTYPE[E]))
+        assert torch.equal(arena[off:off + nb], alone), f"request {i} k={k} E={E}"
+    assert brev_lib.brev_wait_timeouts() == t0
+    del arena, initial
+    torch.cuda.empty_cache()
+
+
 def test_resident_server_restarts_after_idle(brev_lib, oracle_lib, cuda_device):
     """Arrivals further apart than the idle limit: the host stops the kernel
     between them and launches it again; every result is still right."""
