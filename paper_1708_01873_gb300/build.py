@@ -7,6 +7,8 @@ runtime linked statically, so the library loads without a GPU or driver
 """
 from __future__ import annotations
 
+import contextlib
+import fcntl
 import glob
 import os
 import shutil
@@ -47,10 +49,31 @@ def is_stale() -> bool:
     return any(os.path.getmtime(p) > t for p in _inputs())
 
 
+@contextlib.contextmanager
+def _build_lock():
+    """One build at a time per tree: ranks started together (torchrun) all
+    call the build, and their nvcc processes must not write the same object
+    files at once.  The first takes the lock and builds; the others wait,
+    then find the library up to date."""
+    os.makedirs(BUILD, exist_ok=True)
+    with open(os.path.join(BUILD, ".lock"), "w") as fh:
+        fcntl.flock(fh, fcntl.LOCK_EX)
+        try:
+            yield
+        finally:
+            fcntl.flock(fh, fcntl.LOCK_UN)
+
+
 def build_library(force: bool = False, verbose: bool = False) -> str:
     if not force and not is_stale():
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
+    with _build_lock():
+        if not force and not is_stale():
+            return LIB
+        return _compile_and_link(verbose)
+
+
+def _compile_and_link(verbose: bool) -> str:
     cc = nvcc()
     procs = []
     objs = []

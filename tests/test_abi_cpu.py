@@ -169,3 +169,38 @@ def test_shipped_tune_cache_is_valid(brev_lib):
         assert (e["bx"], e["bz"], e.get("order", 0)) in \
             brev_lib.brev_shapes(e["elem_bytes"], bool(e["in_place"]))
         assert e["bx"] + e["bz"] <= e["log2n"]
+
+
+def test_concurrent_builds_compile_once(monkeypatch, tmp_path):
+    """Ranks started together all call the build.  The build takes a file
+    lock and re-checks staleness under it, so one caller compiles and the
+    others find the library up to date; no two compilations overlap.  The
+    compiler is replaced by a recorder here, so nothing is compiled."""
+    import threading
+    import time
+
+    from paper_1708_01873_gb300 import build as B
+
+    monkeypatch.setattr(B, "BUILD", str(tmp_path))
+    state = {"built": False, "active": 0, "max_active": 0, "compiles": 0}
+    guard = threading.Lock()
+
+    def fake_compile(verbose):
+        with guard:
+            state["active"] += 1
+            state["compiles"] += 1
+            state["max_active"] = max(state["max_active"], state["active"])
+        time.sleep(0.2)
+        with guard:
+            state["active"] -= 1
+            state["built"] = True
+        return B.LIB
+
+    monkeypatch.setattr(B, "is_stale", lambda: not state["built"])
+    monkeypatch.setattr(B, "_compile_and_link", fake_compile)
+    threads = [threading.Thread(target=B.build_library) for _ in range(4)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert state["compiles"] == 1 and state["max_active"] == 1
