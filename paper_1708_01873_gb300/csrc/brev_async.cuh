@@ -115,6 +115,16 @@ __device__ __forceinline__ void cp_async16(void* dst_smem, const void* src) {
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
+// The copies this thread issued since its last commit form one group;
+// cp_async_wait_group<N> returns once at most N of its groups (the most
+// recent ones) are still in flight.
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 // Ordered accesses for hand-offs between the host and a running kernel
 // (system scope: page-locked host memory) and between CTAs (GPU scope).

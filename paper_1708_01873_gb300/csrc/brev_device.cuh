@@ -275,10 +275,13 @@ struct Geom {
 // thread): on GB300 the large arrays moved from 0.99 to 1.01 of the
 // measured copy bandwidth.  The element-wide path (W = E, pointers not
 // 16-byte aligned) loads through registers in batches of up to 8 per thread.
-template <class G, bool NC, int NTHR, int NT>
+// WAIT = false (16-byte chunks only) issues the copies and returns: the
+// caller commits them as a group and waits for the group later.
+template <class G, bool NC, int NTHR, int NT, bool WAIT = true>
 __device__ __forceinline__ void load_tiles(typename ChunkT<G::W>::type* sm,
                                            const char* src0, const char* src1,
                                            uint64_t row_stride, int nt_active) {
+  static_assert(WAIT || G::W == 16, "only the asynchronous 16-byte path can defer its wait");
   using C = typename ChunkT<G::W>::type;
   constexpr int PER = (G::CHUNKS + NTHR - 1) / NTHR;  // chunks per thread per tile
   constexpr int TOTAL = PER * NT;
@@ -298,7 +301,7 @@ __device__ __forceinline__ void load_tiles(typename ChunkT<G::W>::type* sm,
                    base + (uint64_t)x * row_stride + (unsigned)c * 16);
       }
     }
-    cp_async_wait_all();
+    if constexpr (WAIT) cp_async_wait_all();
   } else {
 #pragma unroll 1
     for (int b0 = 0; b0 < TOTAL; b0 += BATCH) {

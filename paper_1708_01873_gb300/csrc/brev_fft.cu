@@ -368,6 +368,67 @@ __global__ void __launch_bounds__(fft_ip_threads<E, B>(), fft_ip_min_ctas<E>())
   if (nt == 2) store_tile<G, NTHR>(smem_u4 + G::CHUNKS, ty, stride);
 }
 
+// complex<double> out of place: the FP64 pipe, not HBM, bounds the stages
+// (GB300 issues 2 FP64 operations per SM per cycle), so FP64 work outside
+// the butterflies costs time.  In the one-tile-per-CTA kernel above every
+// CTA spends 2^(B-1) double-precision sincospi on its twiddles (about 0.4
+// FP64 operations per element at B = 5).  The streaming kernel runs one CTA
+// per resident slot: it computes the twiddles once, and the next tile is in
+// flight (cp.async, one commit group per tile, two buffers) while the
+// current tile's stages run and it is stored.  The CTAs of an SM share its
+// FP64 pipe and progress at different speeds, so tiles are claimed from a
+// counter (zeroed in stream order before the launch) rather than dealt out
+// by a fixed stride: CTA c takes tile c first, then gridDim.x + the
+// counter's old value, one claim ahead so that the atomic's round trip
+// overlaps a tile's work.  It is used for 2^5 x 2^5 tiles (the tile of every
+// stage count up to 5 once k >= 10) when there are more tiles than resident
+// slots; two buffers still fit 6 CTAs per SM.  At B = 6 (one CTA per SM) it
+// measured slower, and so did an in-place form with two buffers of tile
+// pairs (3 CTAs per SM).
+template <int B>
+__global__ void __launch_bounds__(fft_oop_threads<16, B>(), BREV_FFT_MIN_CTAS)
+    k_fft_oop_stream(char* __restrict__ dst, const char* __restrict__ src, int k, int S,
+                     int inverse, unsigned* __restrict__ ticket) {
+  constexpr int E = 16;
+  using G = Geom<E, 16, B, B>;
+  constexpr int NTHR = fft_oop_threads<E, B>();
+  using T = typename Cplx<E>::T;
+  extern __shared__ uint4 smem_u4[];
+  __shared__ uint32_t s_claim;
+  T* tw = reinterpret_cast<T*>(smem_u4 + 2 * G::CHUNKS);
+  pdl_release();
+  fill_twiddles<E, B>(tw);
+  pdl_wait();
+  const int wy = k - 2 * B;
+  const uint32_t ntiles = 1u << wy;
+  const uint64_t stride = (uint64_t)E << (k - B);
+  uint32_t y = blockIdx.x;  // the grid is smaller than the tile count
+  if (threadIdx.x == 0) s_claim = gridDim.x + atomicAdd(ticket, 1u);
+  load_tiles<G, true, NTHR, 1, false>(smem_u4, src + ((uint64_t)y << B) * E, nullptr, stride,
+                                      1);
+  cp_async_commit();
+  __syncthreads();
+  uint32_t yn = s_claim;
+  for (int buf = 0; y < ntiles; buf ^= 1) {
+    uint4* const cur = smem_u4 + buf * G::CHUNKS;
+    uint32_t claim = 0;
+    if (yn < ntiles) {  // the other buffer was released by the barrier ending the last tile
+      load_tiles<G, true, NTHR, 1, false>(smem_u4 + (buf ^ 1) * G::CHUNKS,
+                                          src + ((uint64_t)yn << B) * E, nullptr, stride, 1);
+      if (threadIdx.x == 0) claim = atomicAdd(ticket, 1u);  // the tile after yn
+    }
+    cp_async_commit();
+    cp_async_wait_group<1>();  // this tile's group has landed; the next one may be in flight
+    __syncthreads();
+    dit_stages<G, NTHR>(cur, 1, S, inverse, tw);
+    store_tile<G, NTHR>(cur, dst + ((uint64_t)rev_bits(y, wy) << B) * E, stride);
+    if (threadIdx.x == 0) s_claim = yn < ntiles ? gridDim.x + claim : ntiles;
+    __syncthreads();  // every thread has read cur before it is refilled, and sees s_claim
+    y = yn;
+    yn = s_claim;
+  }
+}
+
 // Small arrays (and any array that fits): one CTA stages the permuted array
 // in shared memory, runs the stages, and stores it.
 template <int E>
@@ -411,6 +472,7 @@ __global__ void __launch_bounds__(256) k_fft_small(char* dst, const char* src, i
 struct FftKernel {
   const void* oop;
   const void* inplace;
+  const void* oop_stream;  // complex<double> with B = 5: the streaming form (else nullptr)
   int B, threads, ip_threads;
   unsigned tile_bytes;
 };
@@ -418,8 +480,24 @@ struct FftKernel {
 template <int E, int B>
 static FftKernel fft_k() {
   using G = Geom<E, 16, B, B>;
-  return {(const void*)&k_fft_oop<E, B>, (const void*)&k_fft_inplace<E, B>, B,
-          fft_oop_threads<E, B>(), fft_ip_threads<E, B>(), G::TILE_BYTES};
+  FftKernel K{(const void*)&k_fft_oop<E, B>, (const void*)&k_fft_inplace<E, B>, nullptr, B,
+              fft_oop_threads<E, B>(), fft_ip_threads<E, B>(), G::TILE_BYTES};
+  if constexpr (E == 16 && B == 5) K.oop_stream = (const void*)&k_fft_oop_stream<B>;
+  return K;
+}
+
+// Grid of a streaming kernel: every resident slot of the device, at most
+// one CTA per unit.
+static cudaError_t stream_grid(const void* kern, unsigned threads, unsigned smem,
+                               unsigned long long units, unsigned* grid) {
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (int)threads,
+                                                                smem);
+  if (e != cudaSuccess) return e;
+  const unsigned long long slots =
+      (unsigned long long)std::max(per_sm, 1) * (unsigned long long)current_device_sm_count();
+  *grid = (unsigned)std::min(slots, units);
+  return cudaSuccess;
 }
 
 static bool fft_lookup(int E, int B, FftKernel* out) {
@@ -498,12 +576,37 @@ extern "C" brev_status brev_fft_stages(void* dst, const void* src, int log2n, in
     void* args[] = {(void*)&d, (void*)&kk, (void*)&SS, (void*)&inv};
     e = launch_pdl(K.inplace, (unsigned)grid, K.ip_threads, args, smem, s);
   } else {
-    const unsigned long long grid = 1ull << (k - 2 * K.B);
+    const unsigned long long units = 1ull << (k - 2 * K.B);
+    char* d = (char*)dst;
+    const char* sr = (const char*)src;
+    unsigned grid = (unsigned)units;
+    if (K.oop_stream) {
+      const unsigned smem = 2 * K.tile_bytes + tw_bytes;
+      e = ensure_smem(K.oop_stream, smem);
+      if (e == cudaSuccess) e = stream_grid(K.oop_stream, K.threads, smem, units, &grid);
+      if (e != cudaSuccess) return cuda_error(e, "streaming kernel shape");
+      if (grid < units) {  // more tiles than resident slots: stream them
+        void* ticket = nullptr;
+        e = ws_alloc(&ticket, 16, s);
+        if (e != cudaSuccess) {
+          cudaGetLastError();
+          return set_error(BREV_ERR_OOM, "tile counter: %s", cudaGetErrorString(e));
+        }
+        e = cudaMemsetAsync(ticket, 0, 16, s);
+        if (e == cudaSuccess) {
+          unsigned* t = (unsigned*)ticket;
+          void* args[] = {(void*)&d, (void*)&sr, (void*)&kk, (void*)&SS, (void*)&inv, (void*)&t};
+          e = launch_pdl(K.oop_stream, grid, K.threads, args, smem, s);
+        }
+        ws_free(ticket, s);
+        if (e != cudaSuccess) return cuda_error(e, "fused FFT launch");
+        note_launch();
+        return BREV_OK;
+      }
+    }
     const unsigned smem = K.tile_bytes + tw_bytes;
     e = ensure_smem(K.oop, smem);
     if (e != cudaSuccess) return cuda_error(e, "shared-memory limit");
-    char* d = (char*)dst;
-    const char* sr = (const char*)src;
     void* args[] = {(void*)&d, (void*)&sr, (void*)&kk, (void*)&SS, (void*)&inv};
     e = launch_pdl(K.oop, (unsigned)grid, K.threads, args, smem, s);
   }

@@ -96,6 +96,35 @@ def test_eighth_turn_groups_both_directions(brev_lib, oracle_lib, cuda_device, E
                       f"k={k} S={S} E={E} inplace={inplace} inverse={inverse}")
 
 
+def test_streaming_out_of_place_equals_in_place(brev_lib, oracle_lib, cuda_device):
+    """complex<double> out of place with 2^5 x 2^5 tiles and more tiles than
+    resident slots (k >= 20 on GB300) runs the streaming kernel: one CTA per
+    slot, tiles claimed from a counter, the next tile loaded while the
+    current one is computed.  In place runs the one-unit-per-CTA kernel with
+    the same butterflies, so the two results must be equal byte for byte.
+    The sizes cover the one-tile-per-CTA kernel (k <= 19), a few tiles per
+    CTA (k = 20, 21: most CTAs take one or two claims, the last ones none)
+    and many (k = 23), for every pass split; the smaller ones are also
+    checked against the oracle."""
+    for k in (6, 10, 16, 20, 21, 23):
+        for S in (0, 1, 3, 4, 5):
+            if S > k:
+                continue
+            for inverse in (False, True):
+                seed = 11000 + 10 * k + S + inverse
+                src = device_array(seed, k, 16)
+                out = torch.empty_like(src)
+                brev_lib.brev_fft_stages(out, src, S, inverse)
+                brev_lib.brev_fft_stages(src, src, S, inverse)
+                torch.cuda.synchronize()
+                assert torch.equal(out.view(torch.uint8), src.view(torch.uint8)), \
+                    f"k={k} S={S} inverse={inverse}: out of place differs from in place"
+                if k <= 20:
+                    x = as_complex(host_array(seed, k, 16), 16)
+                    check(to_bytes(out), x, k, 16, S, inverse,
+                          f"k={k} S={S} inverse={inverse}")
+
+
 @pytest.mark.parametrize("E", (8, 16))
 def test_full_fft_small_arrays(brev_lib, oracle_lib, cuda_device, E):
     """All stages in one CTA for arrays that fit: the whole FFT."""
