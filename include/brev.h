@@ -258,7 +258,13 @@ BREV_API brev_status brev_permute_recursive(void *data, int log2n, int elem_byte
  * permutation; stages up to 6 are supported for every size (up to log2n
  * when the whole array fits one CTA); more return BREV_ERR_UNSUPPORTED.
  * Results are floating point: they match a double-precision reference to
- * within rounding (see the tests for the bound). */
+ * within rounding (see the tests for the bound).  complex<double> arrays
+ * with more 2^5 x 2^5 tiles (or tile pairs, in place) than the device has
+ * resident CTA slots for them (log2n >= 20 out of place and >= 21 in
+ * place on GB300, stages <= 5) run one CTA per slot, which
+ * claim tiles from a 16-byte counter taken from the library's workspace
+ * pool in stream order (BREV_ERR_OOM if it cannot be had); the results are
+ * the same bit for bit as with one CTA per tile. */
 BREV_API brev_status brev_fft_stages(void *dst, const void *src, int log2n, int elem_bytes,
                                      int stages, int inverse, void *stream);
 

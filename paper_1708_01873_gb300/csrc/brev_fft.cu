@@ -429,6 +429,70 @@ __global__ void __launch_bounds__(fft_oop_threads<16, B>(), BREV_FFT_MIN_CTAS)
   }
 }
 
+// Tiles (y, rev(y)) of in-place unit q (pairs first, then self-paired tiles).
+__device__ __forceinline__ int fft_unit(uint32_t q, int wy, uint32_t npairs, uint32_t& y,
+                                        uint32_t& ry) {
+  if (q < npairs) {
+    y = unrank_lt(q, wy);
+    ry = rev_bits(y, wy);
+    return 2;
+  }
+  y = ry = unrank_self(q - npairs, wy);
+  return 1;
+}
+
+// complex<double> in place, the same way: one CTA per resident slot,
+// twiddles once per CTA, units (tile pairs, then self-paired tiles) claimed
+// from a counter.  A unit's two tiles are both staged before either is
+// written (the swap through the buffer), and units are disjoint.  One
+// buffer of a pair per CTA keeps 6 CTAs per SM, whose loads and stores
+// overlap each other's stages; two buffers (3 CTAs per SM) measured slower
+// (6.06 against 6.01 ms at k = 28, S = 5).
+template <int B>
+__global__ void __launch_bounds__(fft_ip_threads<16, B>(), BREV_FFT_MIN_CTAS)
+    k_fft_inplace_stream(char* data, int k, int S, int inverse, unsigned* __restrict__ ticket) {
+  constexpr int E = 16;
+  using G = Geom<E, 16, B, B>;
+  constexpr int NTHR = fft_ip_threads<E, B>();
+  using T = typename Cplx<E>::T;
+  extern __shared__ uint4 smem_u4[];
+  __shared__ uint32_t s_claim;
+  T* tw = reinterpret_cast<T*>(smem_u4 + 2 * G::CHUNKS);
+  pdl_release();
+  fill_twiddles<E, B>(tw);
+  pdl_wait();
+  const int wy = k - 2 * B;
+  const uint32_t npairs = count_lt(wy);
+  const uint32_t units = npairs + count_self(wy);
+  const uint64_t stride = (uint64_t)E << (k - B);
+  uint32_t q = blockIdx.x;  // the grid is smaller than the unit count
+  if (threadIdx.x == 0) s_claim = gridDim.x + atomicAdd(ticket, 1u);
+  uint32_t y, ry;
+  int nt = fft_unit(q, wy, npairs, y, ry);
+  load_tiles<G, false, NTHR, 2, false>(smem_u4, data + ((uint64_t)y << B) * E,
+                                       data + ((uint64_t)ry << B) * E, stride, nt);
+  __syncthreads();
+  uint32_t qn = s_claim;
+  while (q < units) {
+    uint32_t claim = 0;
+    if (qn < units && threadIdx.x == 0) claim = atomicAdd(ticket, 1u);  // the unit after qn
+    cp_async_wait_all();
+    __syncthreads();
+    dit_stages<G, NTHR>(smem_u4, nt, S, inverse, tw);
+    store_tile<G, NTHR>(smem_u4, data + ((uint64_t)ry << B) * E, stride);
+    if (nt == 2) store_tile<G, NTHR>(smem_u4 + G::CHUNKS, data + ((uint64_t)y << B) * E, stride);
+    if (threadIdx.x == 0) s_claim = qn < units ? gridDim.x + claim : units;
+    __syncthreads();  // every thread has read the buffer, and sees s_claim
+    q = qn;
+    if (q < units) {
+      nt = fft_unit(q, wy, npairs, y, ry);
+      load_tiles<G, false, NTHR, 2, false>(smem_u4, data + ((uint64_t)y << B) * E,
+                                           data + ((uint64_t)ry << B) * E, stride, nt);
+    }
+    qn = s_claim;
+  }
+}
+
 // Small arrays (and any array that fits): one CTA stages the permuted array
 // in shared memory, runs the stages, and stores it.
 template <int E>
@@ -472,7 +536,8 @@ __global__ void __launch_bounds__(256) k_fft_small(char* dst, const char* src, i
 struct FftKernel {
   const void* oop;
   const void* inplace;
-  const void* oop_stream;  // complex<double> with B = 5: the streaming form (else nullptr)
+  const void* oop_stream;      // complex<double> with B = 5: the streaming forms
+  const void* inplace_stream;  // (else nullptr)
   int B, threads, ip_threads;
   unsigned tile_bytes;
 };
@@ -480,9 +545,12 @@ struct FftKernel {
 template <int E, int B>
 static FftKernel fft_k() {
   using G = Geom<E, 16, B, B>;
-  FftKernel K{(const void*)&k_fft_oop<E, B>, (const void*)&k_fft_inplace<E, B>, nullptr, B,
-              fft_oop_threads<E, B>(), fft_ip_threads<E, B>(), G::TILE_BYTES};
-  if constexpr (E == 16 && B == 5) K.oop_stream = (const void*)&k_fft_oop_stream<B>;
+  FftKernel K{(const void*)&k_fft_oop<E, B>, (const void*)&k_fft_inplace<E, B>, nullptr, nullptr,
+              B, fft_oop_threads<E, B>(), fft_ip_threads<E, B>(), G::TILE_BYTES};
+  if constexpr (E == 16 && B == 5) {
+    K.oop_stream = (const void*)&k_fft_oop_stream<B>;
+    K.inplace_stream = (const void*)&k_fft_inplace_stream<B>;
+  }
   return K;
 }
 
@@ -569,6 +637,32 @@ extern "C" brev_status brev_fft_stages(void* dst, const void* src, int log2n, in
   if (inplace) {
     const int w = k - 2 * K.B;
     const unsigned long long grid = (unsigned long long)count_lt(w) + count_self(w);
+    if (K.inplace_stream) {
+      const unsigned smem = 2 * K.tile_bytes + tw_bytes;
+      unsigned g = 0;
+      e = ensure_smem(K.inplace_stream, smem);
+      if (e == cudaSuccess) e = stream_grid(K.inplace_stream, K.ip_threads, smem, grid, &g);
+      if (e != cudaSuccess) return cuda_error(e, "streaming kernel shape");
+      if (g < grid) {
+        void* ticket = nullptr;
+        e = ws_alloc(&ticket, 16, s);
+        if (e != cudaSuccess) {
+          cudaGetLastError();
+          return set_error(BREV_ERR_OOM, "unit counter: %s", cudaGetErrorString(e));
+        }
+        e = cudaMemsetAsync(ticket, 0, 16, s);
+        if (e == cudaSuccess) {
+          char* d = (char*)dst;
+          unsigned* t = (unsigned*)ticket;
+          void* args[] = {(void*)&d, (void*)&kk, (void*)&SS, (void*)&inv, (void*)&t};
+          e = launch_pdl(K.inplace_stream, g, K.ip_threads, args, smem, s);
+        }
+        ws_free(ticket, s);
+        if (e != cudaSuccess) return cuda_error(e, "fused FFT launch");
+        note_launch();
+        return BREV_OK;
+      }
+    }
     const unsigned smem = 2 * K.tile_bytes + tw_bytes;
     e = ensure_smem(K.inplace, smem);
     if (e != cudaSuccess) return cuda_error(e, "shared-memory limit");

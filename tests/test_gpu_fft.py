@@ -97,15 +97,16 @@ def test_eighth_turn_groups_both_directions(brev_lib, oracle_lib, cuda_device, E
 
 
 def test_streaming_out_of_place_equals_in_place(brev_lib, oracle_lib, cuda_device):
-    """complex<double> out of place with 2^5 x 2^5 tiles and more tiles than
-    resident slots (k >= 20 on GB300) runs the streaming kernel: one CTA per
-    slot, tiles claimed from a counter, the next tile loaded while the
-    current one is computed.  In place runs the one-unit-per-CTA kernel with
-    the same butterflies, so the two results must be equal byte for byte.
-    The sizes cover the one-tile-per-CTA kernel (k <= 19), a few tiles per
-    CTA (k = 20, 21: most CTAs take one or two claims, the last ones none)
-    and many (k = 23), for every pass split; the smaller ones are also
-    checked against the oracle."""
+    """complex<double> with 2^5 x 2^5 tiles and more units than resident
+    slots runs the streaming kernels: one CTA per slot, units claimed from a
+    counter.  Out of place (k >= 20 on GB300) the unit is a tile and the next
+    one is loaded while the current one is computed; in place (k >= 21) the
+    unit is a tile pair, one buffer per CTA.  Both run the same butterflies
+    as the one-unit-per-CTA kernels, so out of place and in place must agree
+    byte for byte at every size: one unit per CTA in both modes (k <= 19),
+    streaming out of place only (k = 20), a few claims per CTA in both
+    (k = 21) and many (k = 23), for every pass split.  Up to k = 21 the
+    results are also checked against the oracle."""
     for k in (6, 10, 16, 20, 21, 23):
         for S in (0, 1, 3, 4, 5):
             if S > k:
@@ -119,7 +120,7 @@ def test_streaming_out_of_place_equals_in_place(brev_lib, oracle_lib, cuda_devic
                 torch.cuda.synchronize()
                 assert torch.equal(out.view(torch.uint8), src.view(torch.uint8)), \
                     f"k={k} S={S} inverse={inverse}: out of place differs from in place"
-                if k <= 20:
+                if k <= 21:
                     x = as_complex(host_array(seed, k, 16), 16)
                     check(to_bytes(out), x, k, 16, S, inverse,
                           f"k={k} S={S} inverse={inverse}")
