@@ -140,17 +140,23 @@ def test_full_fft_small_arrays(brev_lib, oracle_lib, cuda_device, E):
                            atol=tol(E, k) * 4)
 
 
-@pytest.mark.parametrize("k,E,S,inverse", [(26, 8, 6, False), (26, 16, 5, False),
-                                           (27, 8, 5, False), (26, 16, 5, True),
-                                           (25, 8, 6, True)])
-def test_fused_full_size_sampled_blocks(brev_lib, oracle_lib, cuda_device, k, E, S, inverse):
+@pytest.mark.parametrize("k,E,S,inverse,inplace", [
+    (26, 8, 6, False, False), (26, 16, 5, False, False), (27, 8, 5, False, False),
+    (26, 16, 5, True, False), (25, 8, 6, True, False), (26, 16, 5, False, True),
+    # the bench's complex<double> workload (4 GiB), both streaming kernels
+    (28, 16, 5, False, False), (28, 16, 5, True, True)])
+def test_fused_full_size_sampled_blocks(brev_lib, oracle_lib, cuda_device, k, E, S, inverse,
+                                        inplace):
     """After S stages, output block b (2^S elements) is the S-stage result of
     the inputs spaced n / 2^S apart starting at rev_{k-S}(b) (pinned on the
     oracle); sampled blocks are checked against the oracle on those inputs,
-    regenerated from the seed."""
+    regenerated from the seed.  In place the result overwrites the input."""
     seed = 7000 + k
     src = device_array(seed, k, E)
-    out = torch.empty_like(src)
+    if inplace:
+        out = src
+    else:
+        out = torch.empty_like(src)
     brev_lib.brev_fft_stages(out, src, S, inverse)
     torch.cuda.synchronize()
     n, m = 1 << k, 1 << S
