@@ -989,6 +989,81 @@ def test_fused_fft_pair_passes_cover_both_tiles():
                     assert len(seen) == nt << log_groups
 
 
+def _streaming_claims(units, grid, rng, buffers):
+    """The streaming complex<double> FFT kernels' schedule, one CTA per
+    resident slot, run under a random interleaving of the CTAs.  CTA c
+    starts at unit c and claims grid + (the counter's old value) for the
+    unit after it before its first unit is processed; in the loop, while
+    the next unit is valid, thread 0 claims the one after it (an atomic on
+    the shared counter), the CTA processes the current unit, and the claim
+    becomes the next unit (units >= `units` end the loop).  With two
+    buffers (out of place) the next unit's tiles are loaded before the
+    current one is processed; with one (in place) after it.  Returns the
+    units each CTA processed in order, the counter's final value and the
+    load/process log of every CTA."""
+    counter = [0]
+
+    def claim():
+        v = counter[0]
+        counter[0] += 1
+        return grid + v
+
+    def cta(c):
+        log = []
+        q = c
+        qn = claim()  # prologue: thread 0, published by the barrier
+        log.append(("load", q))
+        yield
+        while q < units:
+            nxt = qn < units
+            if nxt and buffers == 2:
+                log.append(("load", qn))
+            cl = claim() if nxt else None
+            yield  # other CTAs run between the claim and its use
+            log.append(("process", q))
+            q, qn = qn, (cl if nxt else units)
+            if q < units and buffers == 1:
+                log.append(("load", q))
+            yield
+        return log
+
+    gens = {c: cta(c) for c in range(grid)}
+    logs = {}
+    while gens:
+        c = int(rng.choice(list(gens)))
+        try:
+            next(gens[c])
+        except StopIteration as stop:
+            logs[c] = stop.value
+            del gens[c]
+    return logs, counter[0]
+
+
+@pytest.mark.parametrize("buffers", (1, 2))
+def test_streaming_fft_claims_cover_each_unit_once(buffers):
+    """Every unit (tile, or tile pair in place) is processed by exactly one
+    CTA, every CTA ends, each CTA loads a unit before processing it and
+    processes what it loaded in the same order.  The counter ends at exactly
+    `units`: the units past the first `grid` are claimed once each, and every
+    CTA makes one failing claim, so grid + counter stays below units + grid
+    and a 32-bit counter cannot wrap for any array the kernels accept."""
+    rng = np.random.default_rng(3)
+    for units, grid in ((913, 912), (1024, 912), (2048, 912), (5000, 456), (40, 7), (8, 7)):
+        for _ in range(3):
+            logs, final = _streaming_claims(units, grid, rng, buffers)
+            assert sorted(logs) == list(range(grid))
+            done = [q for log in logs.values() for op, q in log if op == "process"]
+            assert sorted(done) == list(range(units))
+            for log in logs.values():
+                loaded = [q for op, q in log if op == "load" and q < units]
+                processed = [q for op, q in log if op == "process"]
+                assert loaded == processed
+                for i, (op, q) in enumerate(log):  # loaded before processed
+                    if op == "process":
+                        assert ("load", q) in log[:i]
+            assert final == units
+
+
 class _MBar:
     """mbarrier phase semantics: a phase completes when its pending
     arrivals reach 0 and its transaction bytes are all in; try_wait(P) is
