@@ -264,7 +264,9 @@ BREV_API brev_status brev_permute_recursive(void *data, int log2n, int elem_byte
  * place on GB300, stages <= 5) run one CTA per slot, which
  * claim tiles from a 16-byte counter taken from the library's workspace
  * pool in stream order (BREV_ERR_OOM if it cannot be had); the results are
- * the same bit for bit as with one CTA per tile. */
+ * the same bit for bit as with one CTA per tile.  Everything the call
+ * enqueues (that allocation, a memset, the kernel, the release) can be
+ * captured into a CUDA graph; a GPU test captures and replays it. */
 BREV_API brev_status brev_fft_stages(void *dst, const void *src, int log2n, int elem_bytes,
                                      int stages, int inverse, void *stream);
 

@@ -126,6 +126,42 @@ def test_streaming_out_of_place_equals_in_place(brev_lib, oracle_lib, cuda_devic
                           f"k={k} S={S} inverse={inverse}")
 
 
+def test_streaming_fft_captured_in_graph(brev_lib, cuda_device):
+    """The streaming complex<double> kernels enqueue a stream-ordered
+    allocation of their 16-byte unit counter, its memset, the kernel and the
+    counter's release: all capturable.  Capture each mode once (k = 21, where
+    both modes stream) and replay it twice; every replay equals the eager
+    call byte for byte (in place, the input is restored between replays)."""
+    k, S = 21, 5
+    src = device_array(12000, k, 16)
+    ref = torch.empty_like(src)
+    brev_lib.brev_fft_stages(ref, src, S, False)  # eager: also sets the kernels' smem limits
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    out = torch.empty_like(src)
+    work = src.clone()
+    for inplace in (False, True):
+        g = torch.cuda.CUDAGraph()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=s, capture_error_mode="thread_local"):
+            if inplace:
+                brev_lib.brev_fft_stages(work, work, S, False, stream=s)
+            else:
+                brev_lib.brev_fft_stages(out, src, S, False, stream=s)
+        for replay in range(2):
+            if inplace:
+                work.copy_(src)
+            else:
+                out.zero_()
+            torch.cuda.synchronize()
+            g.replay()
+            torch.cuda.synchronize()
+            got = work if inplace else out
+            assert torch.equal(got.view(torch.uint8), ref.view(torch.uint8)), \
+                f"inplace={inplace} replay {replay}"
+        del g
+
+
 @pytest.mark.parametrize("E", (8, 16))
 def test_full_fft_small_arrays(brev_lib, oracle_lib, cuda_device, E):
     """All stages in one CTA for arrays that fit: the whole FFT."""
