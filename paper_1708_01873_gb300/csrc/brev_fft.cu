@@ -218,6 +218,63 @@ __device__ __forceinline__ void dit_group(T* v, int j, const T* tw) {
   }
 }
 
+// Stages 4 and 5 of a complex<double> group v[t] = X(base + j + 8 t),
+// t < 4, j in {1, 2, 3, 5, 6, 7}, in 22 fused multiply-adds instead of the
+// 24 of four multiply-add butterflies.  With w = exp(-2 pi i j / 32), stage
+// 4 pairs (v0, v1) and (v2, v3) with w^2 and stage 5 pairs the results
+// (A, C) with w and (B, D) with -i w, so
+//   A, B = v0 +- w^2 v1,   w C, w D = w v2 +- w^3 v3,
+//   out0, out2 = A +- w C,   out1, out3 = B -+ i w D.
+// Writing w^m = c_m (1 + i t_m) (t_m = tan, c_m = cos of the angle m j pi / 16):
+// u = (1 + i t2) v1 and p2 = (1 + i t1) v2, p3 = (1 + i t3) v3 take two
+// operations each; A, B = v0 +- c2 u, q+- = p2 +- (c3 / c1) p3 and the
+// outputs A +- c1 q+, B -+ i c1 q- two each, the factor c1 of w C = c1 q+ and
+// w D = c1 q- folding into the last multiply-adds (the multiply-add form of
+// the radix-4 butterfly).  Every c_m is nonzero for these j.  A tangent
+// product is rounded relative to a value at most (1 + |t|) times its input
+// and is then scaled by |c| = 1 / sqrt(1 + t^2), so each error stays within
+// about sqrt(2) ulp of the inputs' magnitude, as in the plain butterfly.
+// kRadix4Fma[j] = {t1, t2, t3, c1, c2, c3 / c1}, each the double nearest the
+// exact value (rows 0 and 4 are unused: those groups take compile-time
+// twiddles).  The index j is the same for a warp's 32 lanes, so the table is
+// read by broadcast.
+__constant__ double kRadix4Fma[8][6] = {
+    {0, 0, 0, 0, 0, 0},
+    {-0.198912367379658, -0.41421356237309503, -0.6681786379192989, 0.9807852804032304,
+     0.9238795325112867, 0.8477590650225735},
+    {-0.41421356237309503, -1.0, -2.414213562373095, 0.9238795325112867, 0.7071067811865476,
+     0.41421356237309503},
+    {-0.6681786379192989, -2.414213562373095, 5.027339492125848, 0.8314696123025452,
+     0.3826834323650898, -0.23463313526982046},
+    {0, 0, 0, 0, 0, 0},
+    {-1.496605762665489, 2.414213562373095, 0.198912367379658, 0.5555702330196022,
+     -0.3826834323650898, -1.7653668647301795},
+    {-2.414213562373095, 1.0, -0.41421356237309503, 0.3826834323650898, -0.7071067811865476,
+     -2.414213562373095},
+    {-5.027339492125848, 0.41421356237309503, -1.496605762665489, 0.19509032201612828,
+     -0.9238795325112867, -2.8477590650225735},
+};
+
+__device__ __forceinline__ void radix4_fma(double2* v, int j) {
+  const double t1 = kRadix4Fma[j][0], t2 = kRadix4Fma[j][1], t3 = kRadix4Fma[j][2];
+  const double c1 = kRadix4Fma[j][3], c2 = kRadix4Fma[j][4], r = kRadix4Fma[j][5];
+  const double ux = fmad(-t2, v[1].y, v[1].x), uy = fmad(t2, v[1].x, v[1].y);
+  const double ax = fmad(c2, ux, v[0].x), ay = fmad(c2, uy, v[0].y);
+  const double bx = fmad(-c2, ux, v[0].x), by = fmad(-c2, uy, v[0].y);
+  const double p2x = fmad(-t1, v[2].y, v[2].x), p2y = fmad(t1, v[2].x, v[2].y);
+  const double p3x = fmad(-t3, v[3].y, v[3].x), p3y = fmad(t3, v[3].x, v[3].y);
+  const double qpx = fmad(r, p3x, p2x), qpy = fmad(r, p3y, p2y);
+  const double qmx = fmad(-r, p3x, p2x), qmy = fmad(-r, p3y, p2y);
+  v[0].x = fmad(c1, qpx, ax);
+  v[0].y = fmad(c1, qpy, ay);
+  v[2].x = fmad(-c1, qpx, ax);
+  v[2].y = fmad(-c1, qpy, ay);
+  v[1].x = fmad(c1, qmy, bx);   // B - i c1 q-
+  v[1].y = fmad(-c1, qmx, by);
+  v[3].x = fmad(-c1, qmy, bx);  // B + i c1 q-
+  v[3].y = fmad(c1, qmx, by);
+}
+
 // Stages 4 .. 3 + R (R <= 3) on every output row of a staged tile, in
 // registers, after the first pass took stages 1..3 (rows hold at most 2^6
 // elements, so this is the last pass): each thread takes groups of 2^R
@@ -248,6 +305,7 @@ __device__ __forceinline__ void dit_pass(uint4* sm0, int nt, uint32_t conj_out,
     for (int t = 0; t < GN; ++t) v[t] = *tile_elem<G>(sm, base + j + (t << S0), z);
     if (j == 0) dit_group<G, R, S0, 0>(v, j, tw);
     else if (j == 4) dit_group<G, R, S0, 4>(v, j, tw);
+    else if constexpr (R == 2 && sizeof(typename Cplx<G::E>::R) == 8) radix4_fma(v, j);
     else dit_group<G, R, S0, -1>(v, j, tw);
 #pragma unroll
     for (int t = 0; t < GN; ++t) {

@@ -901,11 +901,67 @@ def _bfly_const(a, b, S, JJ):
     return px + 1j * py, (2 * a.real - px) + 1j * (2 * a.imag - py)
 
 
+def _radix4_table():
+    """kRadix4Fma as written in brev_fft.cu: row j = {t1, t2, t3, c1, c2,
+    c3 / c1}."""
+    import os
+    import re
+    src = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                            "paper_1708_01873_gb300", "csrc", "brev_fft.cu")).read()
+    body = re.search(r"kRadix4Fma\[8\]\[6\] = \{(.*?)\};", src, re.S).group(1)
+    rows = re.findall(r"\{([^{}]*)\}", body)
+    return [[float(x) for x in r.split(",")] for r in rows]
+
+
+def _radix4_fma(v, K):
+    """radix4_fma restated: stages 4 and 5 of a group v0..v3 (positions j +
+    8 t) in the tangent form w^m = c_m (1 + i t_m)."""
+    t1, t2, t3, c1, c2, r = K
+    u = v[1] + 1j * t2 * v[1]
+    A, Bv = v[0] + c2 * u, v[0] - c2 * u
+    p2, p3 = v[2] + 1j * t1 * v[2], v[3] + 1j * t3 * v[3]
+    qp, qm = p2 + r * p3, p2 - r * p3
+    return [A + c1 * qp, Bv - 1j * c1 * qm, A - c1 * qp, Bv + 1j * c1 * qm]
+
+
+def test_radix4_constants_are_the_closed_forms():
+    """Each entry of the kernels' radix-4 table is the double nearest its
+    definition (exactly, against 50-digit arithmetic when mpmath is there;
+    within 1e-15 relative of numpy's libm values in any case), rows 0 and 4 are
+    unused, and the tangent form reproduces w^m: c_m (1 + i t_m) = w^m."""
+    K = _radix4_table()
+    assert len(K) == 8 and all(len(r) == 6 for r in K)
+    assert K[0] == [0.0] * 6 and K[4] == [0.0] * 6
+    try:
+        import mpmath as mp
+    except ImportError:
+        mp = None
+    for j in (1, 2, 3, 5, 6, 7):
+        th = -np.pi * j / 16
+        if mp is not None:
+            with mp.workdps(50):
+                a = -mp.pi * j / 16
+                exact = [mp.tan(a), mp.tan(2 * a), mp.tan(3 * a), mp.cos(a), mp.cos(2 * a),
+                         mp.cos(3 * a) / mp.cos(a)]
+                assert K[j] == [float(x) for x in exact], j
+        want = [np.tan(th), np.tan(2 * th), np.tan(3 * th), np.cos(th), np.cos(2 * th),
+                np.cos(3 * th) / np.cos(th)]
+        for got, w in zip(K[j], want):  # numpy's angle 3 th is itself rounded
+            assert abs(got - w) <= 1e-15 * max(1.0, abs(w)), (j, got, w)
+        w = np.exp(1j * th)
+        t1, t2, t3, c1, c2, r = K[j]
+        assert abs(c1 * (1 + 1j * t1) - w) < 1e-15
+        assert abs(c2 * (1 + 1j * t2) - w ** 2) < 1e-15
+        assert abs(r * c1 * (1 + 1j * t3) - w ** 3) < 1e-15
+
+
 def test_fused_fft_multiply_add_butterflies():
     """The kernels' arithmetic forms -- forward butterflies only, with
     compile-time twiddles in the first pass (w = 1, quarter and eighth turns)
     and table twiddles with the double-precision multiply-add butterfly after
-    it (complex<float> keeps the textbook butterfly emulated above); the
+    it, or, for the second pass's radix-4 groups with j not 0 or 4, the
+    22-operation tangent form (complex<float> keeps the textbook butterfly
+    emulated above); the
     inverse conjugates the imaginary parts on the first pass's loads and the
     last pass's stores -- give the textbook DIT stages with
     w = exp(-+2 pi i j / 2^s) for every B and S, both directions."""
@@ -939,6 +995,11 @@ def test_fused_fft_multiply_add_butterflies():
                         base = (q >> s0) << (s0 + R)
                         Xs = [base + j + (t << s0) for t in range(1 << R)]
                         v = [got[:, X].copy() for X in Xs]
+                        if R == 2 and j not in (0, 4):  # radix4_fma (double precision)
+                            v = _radix4_fma(v, _radix4_table()[j])
+                            for X, val in zip(Xs, v):
+                                got[:, X] = last(val)
+                            continue
                         for r in range(R):
                             s = s0 + r + 1
                             hmask = (1 << (s - 1)) - 1
