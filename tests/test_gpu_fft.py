@@ -180,7 +180,9 @@ def test_full_fft_small_arrays(brev_lib, oracle_lib, cuda_device, E):
     (26, 8, 6, False, False), (26, 16, 5, False, False), (27, 8, 5, False, False),
     (26, 16, 5, True, False), (25, 8, 6, True, False), (26, 16, 5, False, True),
     # the bench's complex<double> workload (4 GiB), both streaming kernels
-    (28, 16, 5, False, False), (28, 16, 5, True, True)])
+    (28, 16, 5, False, False), (28, 16, 5, True, True),
+    # the largest array the call accepts (k = 31, 32 GiB), in place
+    (31, 16, 5, False, True)])
 def test_fused_full_size_sampled_blocks(brev_lib, oracle_lib, cuda_device, k, E, S, inverse,
                                         inplace):
     """After S stages, output block b (2^S elements) is the S-stage result of
